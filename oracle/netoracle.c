@@ -1,0 +1,427 @@
+/*
+ * netoracle.c -- plain FP64 CPU oracle for the Kirchhoff network solve.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline / reference leg may load this library.  The CUDA
+ * solver never calls it and shares no code with it.
+ *
+ * What it computes (Dashtian & Sahimi, arXiv:1908.03301):
+ *   * Sec. II: a square (2D) or cubic (3D) bond network; bond ij has
+ *     conductance g_ij and carries flow q_ij = g_ij (P_j - P_i).
+ *   * Eq. 3:   mass balance sum_j q_ij = 0 at every interior node gives the
+ *     linear system G P = b; b collects the bonds to the fixed-pressure faces.
+ *   * Sec. II: a fixed pressure drop along one axis (faces x_f = 0 at p_in and
+ *     x_f = n_f-1 at p_out).  The transverse boundaries are no-flow (the
+ *     planes simply have no bond beyond the last node).
+ *   * Eq. 4:   K = (Q/S)(mu L / dP) with Q the total inlet flow, in lattice
+ *     units mu = 1, L = n_f - 1, S = product of the transverse node counts.
+ *   * Sec. II / IV: G P = b solved by conjugate gradients; the preconditioner
+ *     is Jacobi (z = D^-1 r), the textbook preconditioned CG.
+ *
+ * Clusters (the paper is silent; this is the reading used throughout): nodes
+ * joined by open bonds (g > 0) among interior nodes form clusters.  A cluster
+ * with open bonds to both faces is "spanning" and is the only part solved.
+ * A cluster touching only the inlet face has P = p_in, only the outlet face
+ * P = p_out (no current flows in either), an isolated cluster P = 0.  The
+ * canonical cluster label is the smallest linear node index in the cluster;
+ * inlet-face nodes carry label -1 and outlet-face nodes -2.
+ *
+ * Layout: node (x,y,z) has linear index x + nx*(y + ny*z).  Bond plane d holds
+ * the bond from node c to c + e_d; its extents are the node extents with n_d
+ * reduced by one, indexed the same way.
+ *
+ * Sums over nodes use a fixed split into ORC_NCHUNK pieces added in order, so
+ * results do not depend on the OpenMP thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_NCHUNK 64
+
+typedef struct {
+    int ndim;          /* 2 or 3 */
+    int64_t n[3];      /* node extents; n[2] = 1 in 2D */
+    int flow_axis;     /* axis of the imposed pressure drop */
+    double p_in, p_out;
+} or_desc;
+
+typedef struct {
+    double g_eff;         /* Q_in / (p_in - p_out) */
+    double k_eff;         /* Eq. 4 in lattice units */
+    double q_in, q_out;   /* total flow through the inlet / outlet faces */
+    double rel_residual;  /* ||b - G P||_2 / ||b||_2 (true residual) */
+    double max_imbalance; /* max_i |b - G P|_i over solved nodes */
+    double energy_g;      /* sum_bonds g dP_b^2 / (p_in - p_out)^2 */
+    int64_t n_active;     /* nodes of the spanning cluster(s) */
+    int64_t iters;        /* CG iterations */
+    int status;           /* 0 ok, 1 not converged, -1 invalid input */
+} or_result;
+
+enum { CLS_ISOLATED = 0, CLS_INLET = 1, CLS_OUTLET = 2, CLS_SPANNING = 3,
+       CLS_FACE_IN = 4, CLS_FACE_OUT = 5 };
+
+/* ------------------------------------------------------------------ */
+/* lattice helpers                                                     */
+/* ------------------------------------------------------------------ */
+static int64_t n_nodes(const or_desc *d) { return d->n[0] * d->n[1] * d->n[2]; }
+
+static void coords(const or_desc *d, int64_t i, int64_t c[3]) {
+    c[0] = i % d->n[0];
+    c[1] = (i / d->n[0]) % d->n[1];
+    c[2] = i / (d->n[0] * d->n[1]);
+}
+
+static int64_t node_index(const or_desc *d, const int64_t c[3]) {
+    return c[0] + d->n[0] * (c[1] + d->n[1] * c[2]);
+}
+
+/* Conductance of the bond from node c to c + e_dir (the bond must exist). */
+static double bond(const or_desc *d, const double *const g[3], int dir, const int64_t c[3]) {
+    int64_t m0 = d->n[0] - (dir == 0), m1 = d->n[1] - (dir == 1);
+    return g[dir][c[0] + m0 * (c[1] + m1 * c[2])];
+}
+
+/* 0 = interior unknown, 1 = inlet face, 2 = outlet face */
+static int node_kind(const or_desc *d, const int64_t c[3]) {
+    int64_t cf = c[d->flow_axis];
+    if (cf == 0) return 1;
+    if (cf == d->n[d->flow_axis] - 1) return 2;
+    return 0;
+}
+
+/*
+ * Enumerate the (up to 2*ndim) neighbours of node c.  For k in [0, 2*ndim):
+ * direction k/2, sign + for even k.  Returns 0 if that neighbour does not
+ * exist, else 1 with *j its index and *gij the bond conductance.
+ */
+static int neighbour(const or_desc *d, const double *const g[3], const int64_t c[3], int k,
+                     int64_t *j, double *gij) {
+    int dir = k / 2;
+    int64_t cc[3] = {c[0], c[1], c[2]};
+    if ((k & 1) == 0) {
+        if (c[dir] + 1 >= d->n[dir]) return 0;
+        *gij = bond(d, g, dir, c);
+        cc[dir] += 1;
+    } else {
+        if (c[dir] == 0) return 0;
+        cc[dir] -= 1;
+        *gij = bond(d, g, dir, cc);
+    }
+    *j = node_index(d, cc);
+    return 1;
+}
+
+static int validate(const or_desc *d, const double *const g[3]) {
+    if (!d || (d->ndim != 2 && d->ndim != 3)) return -1;
+    for (int a = 0; a < 3; a++)
+        if (d->n[a] < 1) return -1;
+    if (d->ndim == 2 && d->n[2] != 1) return -1;
+    if (d->flow_axis < 0 || d->flow_axis >= d->ndim) return -1;
+    if (d->n[d->flow_axis] < 3) return -1;
+    if (!isfinite(d->p_in) || !isfinite(d->p_out)) return -1;
+    if (n_nodes(d) >= ((int64_t)1 << 31)) return -1;
+    for (int dir = 0; dir < d->ndim; dir++) {
+        int64_t m = 1;
+        for (int a = 0; a < 3; a++) m *= d->n[a] - (a == dir);
+        for (int64_t b = 0; b < m; b++) {
+            double v = g[dir][b];
+            if (!(v >= 0.0) || !isfinite(v)) return -1;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* cluster labels                                                      */
+/* ------------------------------------------------------------------ */
+static int64_t uf_find(int64_t *parent, int64_t i) {
+    while (parent[i] != i) {
+        parent[i] = parent[parent[i]];
+        i = parent[i];
+    }
+    return i;
+}
+
+/* The root of a merged set is the smaller of the two roots, so every root is
+ * the smallest index of its set. */
+static void uf_union(int64_t *parent, int64_t a, int64_t b) {
+    int64_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    if (ra == rb) return;
+    if (ra < rb) parent[rb] = ra;
+    else parent[ra] = rb;
+}
+
+/*
+ * Cluster labels and classes.  label[i]: smallest node index of i's cluster
+ * (interior nodes), -1 (inlet face), -2 (outlet face).  cls[i]: bit 0 = the
+ * cluster has an open bond to the inlet face, bit 1 = to the outlet face;
+ * face nodes get CLS_FACE_IN / CLS_FACE_OUT.  Returns 0, or -1 on bad input.
+ */
+int or_labels(const or_desc *d, const double *const g[3], int32_t *label, uint8_t *cls) {
+    if (validate(d, g)) return -1;
+    int64_t N = n_nodes(d);
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    uint8_t *flags = (uint8_t *)calloc((size_t)N, 1);
+    if (!parent || !flags) {
+        free(parent);
+        free(flags);
+        return -1;
+    }
+    for (int64_t i = 0; i < N; i++) parent[i] = i;
+    int64_t c[3], j;
+    double gij;
+    for (int64_t i = 0; i < N; i++) {
+        coords(d, i, c);
+        if (node_kind(d, c) != 0) continue;
+        for (int k = 0; k < 2 * d->ndim; k += 2) { /* + neighbours only: each bond once */
+            if (!neighbour(d, g, c, k, &j, &gij) || !(gij > 0.0)) continue;
+            int64_t cj[3];
+            coords(d, j, cj);
+            if (node_kind(d, cj) == 0) uf_union(parent, i, j);
+        }
+    }
+    for (int64_t i = 0; i < N; i++) {
+        coords(d, i, c);
+        int kind = node_kind(d, c);
+        if (kind == 1) { label[i] = -1; continue; }
+        if (kind == 2) { label[i] = -2; continue; }
+        int64_t r = uf_find(parent, i);
+        label[i] = (int32_t)r;
+        for (int k = 0; k < 2 * d->ndim; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij) || !(gij > 0.0)) continue;
+            int64_t cj[3];
+            coords(d, j, cj);
+            int kj = node_kind(d, cj);
+            if (kj == 1) flags[r] |= 1;
+            if (kj == 2) flags[r] |= 2;
+        }
+    }
+    for (int64_t i = 0; i < N; i++) {
+        if (label[i] == -1) cls[i] = CLS_FACE_IN;
+        else if (label[i] == -2) cls[i] = CLS_FACE_OUT;
+        else cls[i] = flags[label[i]];
+    }
+    free(parent);
+    free(flags);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* vector helpers (fixed-order sums)                                   */
+/* ------------------------------------------------------------------ */
+static double dot(const double *a, const double *b, int64_t n) {
+    double part[ORC_NCHUNK];
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < ORC_NCHUNK; ch++) {
+        int64_t lo = n * ch / ORC_NCHUNK, hi = n * (ch + 1) / ORC_NCHUNK;
+        double s = 0.0;
+        for (int64_t i = lo; i < hi; i++) s += a[i] * b[i];
+        part[ch] = s;
+    }
+    double s = 0.0;
+    for (int ch = 0; ch < ORC_NCHUNK; ch++) s += part[ch];
+    return s;
+}
+
+/*
+ * Nodal current imbalance of a full pressure field P (face nodes included):
+ * out_i = sum_{open j} g_ij (P_j - P_i) for interior nodes, 0 on the faces.
+ * This is (b - G P)_i of Eq. 3 once P holds the face pressures.
+ */
+int or_residual(const or_desc *d, const double *const g[3], const double *P, double *out) {
+    if (validate(d, g)) return -1;
+    int64_t N = n_nodes(d);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+        int64_t c[3], j;
+        double gij, s = 0.0;
+        coords(d, i, c);
+        if (node_kind(d, c) != 0) { out[i] = 0.0; continue; }
+        for (int k = 0; k < 2 * d->ndim; k++)
+            if (neighbour(d, g, c, k, &j, &gij)) s += gij * (P[j] - P[i]);
+        out[i] = s;
+    }
+    return 0;
+}
+
+/*
+ * y = G v restricted to the solved (active) nodes: for active i,
+ * y_i = D_i v_i - sum_{active j} g_ij v_j, with D_i the sum of all open bonds at
+ * i (bonds to face nodes included).  y_i = 0 elsewhere.
+ */
+static void apply_G(const or_desc *d, const double *const g[3], const uint8_t *active,
+                    const double *D, const double *v, double *y) {
+    int64_t N = n_nodes(d);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+        if (!active[i]) { y[i] = 0.0; continue; }
+        int64_t c[3], j;
+        double gij, s = D[i] * v[i];
+        coords(d, i, c);
+        for (int k = 0; k < 2 * d->ndim; k++)
+            if (neighbour(d, g, c, k, &j, &gij) && active[j]) s -= gij * v[j];
+        y[i] = s;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* the solve                                                           */
+/* ------------------------------------------------------------------ */
+/*
+ * Solve Eq. 3 on the spanning cluster with Jacobi-preconditioned CG to
+ * ||b - G P||_2 <= tol ||b||_2, starting from the linear pressure profile
+ * along the flow axis; then the flows and Eq. 4.
+ *
+ *   P     [out] N pressures (faces and non-spanning clusters included).
+ *   label [out, optional] N cluster labels; cls [out, optional] N classes.
+ * nthreads <= 0 keeps the OpenMP default.  Returns res->status.
+ */
+int or_solve(const or_desc *d, const double *const g[3], double tol, int64_t max_iter,
+             int nthreads, double *P, int32_t *label_out, uint8_t *cls_out, or_result *res) {
+    memset(res, 0, sizeof(*res));
+    if (validate(d, g)) { res->status = -1; return -1; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int64_t N = n_nodes(d);
+    int f = d->flow_axis;
+    double dP = d->p_in - d->p_out;
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    uint8_t *cls = (uint8_t *)malloc((size_t)N);
+    uint8_t *active = (uint8_t *)malloc((size_t)N);
+    double *D = (double *)calloc((size_t)N, sizeof(double));
+    double *b = (double *)calloc((size_t)N, sizeof(double));
+    double *x = (double *)calloc((size_t)N, sizeof(double));
+    double *r = (double *)calloc((size_t)N, sizeof(double));
+    double *z = (double *)calloc((size_t)N, sizeof(double));
+    double *p = (double *)calloc((size_t)N, sizeof(double));
+    double *q = (double *)calloc((size_t)N, sizeof(double));
+    if (!label || !cls || !active || !D || !b || !x || !r || !z || !p || !q) {
+        res->status = -1;
+        goto done;
+    }
+    or_labels(d, g, label, cls);
+
+    /* initial pressures: faces, linear profile on the spanning cluster,
+     * face pressure on one-sided clusters, 0 on isolated ones */
+    int64_t n_active = 0;
+    for (int64_t i = 0; i < N; i++) {
+        int64_t c[3];
+        coords(d, i, c);
+        active[i] = (cls[i] == CLS_SPANNING);
+        n_active += active[i];
+        switch (cls[i]) {
+        case CLS_FACE_IN: case CLS_INLET: P[i] = d->p_in; break;
+        case CLS_FACE_OUT: case CLS_OUTLET: P[i] = d->p_out; break;
+        case CLS_SPANNING:
+            P[i] = d->p_in - dP * (double)c[f] / (double)(d->n[f] - 1);
+            break;
+        default: P[i] = 0.0;
+        }
+    }
+    res->n_active = n_active;
+
+    /* diagonal D and right-hand side b of Eq. 3 */
+    for (int64_t i = 0; i < N; i++) {
+        if (!active[i]) continue;
+        int64_t c[3], j;
+        double gij;
+        coords(d, i, c);
+        for (int k = 0; k < 2 * d->ndim; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij)) continue;
+            D[i] += gij;
+            if (!active[j]) b[i] += gij * P[j]; /* an open bond from an active
+                                                   node leads only to the
+                                                   cluster or to a face */
+        }
+        x[i] = P[i];
+    }
+
+    double bnorm = sqrt(dot(b, b, N));
+    /* Jacobi-preconditioned CG */
+    apply_G(d, g, active, D, x, q);
+    for (int64_t i = 0; i < N; i++) r[i] = active[i] ? b[i] - q[i] : 0.0;
+    for (int64_t i = 0; i < N; i++) z[i] = active[i] ? r[i] / D[i] : 0.0;
+    memcpy(p, z, sizeof(double) * (size_t)N);
+    double rz = dot(r, z, N);
+    int64_t it = 0;
+    int converged = (bnorm == 0.0);
+    while (!converged && it < max_iter) {
+        if (sqrt(dot(r, r, N)) <= tol * bnorm) { converged = 1; break; }
+        apply_G(d, g, active, D, p, q);
+        double alpha = rz / dot(p, q, N);
+        for (int64_t i = 0; i < N; i++) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            z[i] = active[i] ? r[i] / D[i] : 0.0;
+        }
+        double rz_new = dot(r, z, N);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = 0; i < N; i++) p[i] = z[i] + beta * p[i];
+        it++;
+    }
+    if (!converged && sqrt(dot(r, r, N)) <= tol * bnorm) converged = 1;
+    res->iters = it;
+    for (int64_t i = 0; i < N; i++)
+        if (active[i]) P[i] = x[i];
+
+    /* true residual of Eq. 3 on the solved nodes */
+    or_residual(d, g, P, r);
+    double rr = 0.0, rmax = 0.0;
+    for (int64_t i = 0; i < N; i++) {
+        if (!active[i]) continue;
+        rr += r[i] * r[i];
+        if (fabs(r[i]) > rmax) rmax = fabs(r[i]);
+    }
+    res->rel_residual = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    res->max_imbalance = rmax;
+
+    /* flows through the faces (Eq. 4's Q) and the dissipated power */
+    double qin = 0.0, qout = 0.0, energy = 0.0;
+    for (int64_t i = 0; i < N; i++) {
+        int64_t c[3], j;
+        double gij;
+        coords(d, i, c);
+        int ki = node_kind(d, c);
+        for (int k = 0; k < 2 * d->ndim; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij)) continue;
+            int64_t cj[3];
+            coords(d, j, cj);
+            int kj = node_kind(d, cj);
+            if (ki == 0 && kj == 1) qin += gij * (P[j] - P[i]);
+            if (ki == 0 && kj == 2) qout += gij * (P[i] - P[j]);
+            if ((k & 1) == 0) energy += gij * (P[i] - P[j]) * (P[i] - P[j]);
+        }
+    }
+    double S = 1.0;
+    for (int a = 0; a < d->ndim; a++)
+        if (a != f) S *= (double)d->n[a];
+    res->q_in = qin;
+    res->q_out = qout;
+    res->g_eff = qin / dP;
+    res->k_eff = res->g_eff * (double)(d->n[f] - 1) / S;
+    res->energy_g = energy / (dP * dP);
+    res->status = converged ? 0 : 1;
+    if (label_out) memcpy(label_out, label, sizeof(int32_t) * (size_t)N);
+    if (cls_out) memcpy(cls_out, cls, (size_t)N);
+done:
+    free(label); free(cls); free(active); free(D); free(b);
+    free(x); free(r); free(z); free(p); free(q);
+    return res->status;
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

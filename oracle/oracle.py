@@ -1,0 +1,149 @@
+"""ctypes front end of the plain-C FP64 oracle (``netoracle.c``).
+
+Test infrastructure: the CUDA solver never imports this module.
+
+Input conventions match the rest of the project: ``dims = (nx, ny[, nz])``,
+bond planes as numpy arrays of shape node-shape with the extent along their own
+direction reduced by one (x fastest, numpy order (z, y, x)).  Planes of any
+float dtype are widened to float64 exactly before the call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "netoracle.c")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+CLS_ISOLATED, CLS_INLET, CLS_OUTLET, CLS_SPANNING, CLS_FACE_IN, CLS_FACE_OUT = range(6)
+
+
+class _Desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 3), ("flow_axis", C.c_int),
+                ("p_in", C.c_double), ("p_out", C.c_double)]
+
+
+class _Res(C.Structure):
+    _fields_ = [("g_eff", C.c_double), ("k_eff", C.c_double), ("q_in", C.c_double),
+                ("q_out", C.c_double), ("rel_residual", C.c_double),
+                ("max_imbalance", C.c_double), ("energy_g", C.c_double),
+                ("n_active", C.c_int64), ("iters", C.c_int64), ("status", C.c_int)]
+
+
+@dataclass
+class OracleResult:
+    g_eff: float
+    k_eff: float
+    q_in: float
+    q_out: float
+    rel_residual: float
+    max_imbalance: float
+    energy_g: float
+    n_active: int
+    iters: int
+    status: int
+    P: np.ndarray
+    label: np.ndarray
+    cls: np.ndarray
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP) into oracle/_build."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                           SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        dp3 = C.POINTER(C.c_double) * 3
+        lib.or_labels.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p, C.c_void_p]
+        lib.or_labels.restype = C.c_int
+        lib.or_residual.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p, C.c_void_p]
+        lib.or_residual.restype = C.c_int
+        lib.or_solve.argtypes = [C.POINTER(_Desc), dp3, C.c_double, C.c_int64, C.c_int,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Res)]
+        lib.or_solve.restype = C.c_int
+        lib.or_max_threads.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _prep(dims, planes, flow_axis, p_in, p_out):
+    ndim = len(dims)
+    n = list(int(v) for v in dims) + [1] * (3 - ndim)
+    desc = _Desc(ndim, (C.c_int64 * 3)(*n), int(flow_axis), float(p_in), float(p_out))
+    arrs = []
+    for d in range(ndim):
+        want = list(n)
+        want[d] -= 1
+        a = np.ascontiguousarray(planes[d], dtype=np.float64)
+        if a.size != int(np.prod(want)):
+            raise ValueError(f"bond plane {d} has {a.size} entries, expected {int(np.prod(want))}")
+        arrs.append(a)
+    while len(arrs) < 3:
+        arrs.append(np.zeros(1))
+    ptrs = (C.POINTER(C.c_double) * 3)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+    N = int(np.prod(n))
+    shape = tuple(reversed(n[:ndim]))
+    return desc, ptrs, arrs, N, shape
+
+
+def labels(dims, planes, flow_axis=0):
+    """Canonical cluster labels (int32) and classes (uint8), node-shaped."""
+    lib = _load()
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    lab = np.empty(N, np.int32)
+    cls = np.empty(N, np.uint8)
+    if lib.or_labels(C.byref(desc), ptrs, lab.ctypes.data, cls.ctypes.data) != 0:
+        raise ValueError("invalid network")
+    return lab.reshape(shape), cls.reshape(shape)
+
+
+def residual(dims, planes, P, flow_axis=0):
+    """Nodal imbalance sum_j g_ij (P_j - P_i) at interior nodes (0 on faces)."""
+    lib = _load()
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    Pc = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
+    out = np.empty(N, np.float64)
+    if lib.or_residual(C.byref(desc), ptrs, Pc.ctypes.data, out.ctypes.data) != 0:
+        raise ValueError("invalid network")
+    return out.reshape(shape)
+
+
+def solve(dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, tol=1e-13, max_iter=10**7,
+          nthreads=0) -> OracleResult:
+    """FP64 Jacobi-PCG solve of Eq. 3 plus the flows of Eq. 4."""
+    lib = _load()
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, p_in, p_out)
+    P = np.empty(N, np.float64)
+    lab = np.empty(N, np.int32)
+    cls = np.empty(N, np.uint8)
+    res = _Res()
+    lib.or_solve(C.byref(desc), ptrs, float(tol), int(max_iter), int(nthreads),
+                 P.ctypes.data, lab.ctypes.data, cls.ctypes.data, C.byref(res))
+    if res.status < 0:
+        raise ValueError("invalid network")
+    return OracleResult(res.g_eff, res.k_eff, res.q_in, res.q_out, res.rel_residual,
+                        res.max_imbalance, res.energy_g, int(res.n_active), int(res.iters),
+                        int(res.status), P.reshape(shape), lab.reshape(shape),
+                        cls.reshape(shape))
+
+
+def max_threads() -> int:
+    return int(_load().or_max_threads())

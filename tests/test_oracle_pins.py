@@ -1,0 +1,247 @@
+"""Pins for the FP64 CPU oracle: closed forms, hand-solved fixtures, a dense
+direct solve, brute-force cluster labels and the invariants of Eq. 3 / Eq. 4.
+
+None of these re-use the oracle's code path; each would fail on a plausible
+slip inside it (a dropped face bond, a sign, a transposed plane index).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_03301_gb300 import netgen
+from tests import _independent as ind
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("dims,f", [((17, 9), 0), ((9, 17), 1), ((5, 6, 7), 0),
+                                     ((5, 6, 7), 1), ((5, 6, 7), 2), ((3, 3), 0)])
+def test_uniform_lattice_closed_form(dims, f):
+    """Uniform g: P is linear along the flow axis and G = g S / R (Eq. 3, Eq. 4)."""
+    g = 2.5
+    r = oracle.solve(dims, netgen.uniform(dims, g), flow_axis=f, p_in=3.0, p_out=-1.0)
+    R = dims[f] - 1
+    S = int(np.prod(dims)) // dims[f]
+    assert rel(r.g_eff, g * S / R) < 1e-12
+    assert rel(r.k_eff, g) < 1e-12
+    xs, ys, zs, _ = ind.node_coords(dims)
+    c = [xs, ys, zs][f]
+    want = 3.0 - 4.0 * c / R
+    np.testing.assert_allclose(r.P.reshape(-1), want, rtol=0, atol=1e-12)
+
+
+def test_stratified_along_layers_arithmetic_mean():
+    """Flow along the layers: G_x = sum_y s_y / (nx - 1) (Wiener upper bound)."""
+    gen = netgen.rng(11)
+    dims = (23, 31)
+    planes, s = netgen.stratified_layers(dims, gen, 1.0)
+    r = oracle.solve(dims, planes, flow_axis=0)
+    assert rel(r.g_eff, s.sum() / (dims[0] - 1)) < 1e-11
+
+
+def test_stratified_across_layers_harmonic_mean():
+    """Flow across the layers: G_y = nx / sum_j 1/t_j (Wiener lower bound)."""
+    gen = netgen.rng(12)
+    dims = (19, 29)
+    planes, s = netgen.stratified_layers(dims, gen, 1.0)
+    t = s[:-1]  # vertical bond between rows j and j+1 carries s_j
+    r = oracle.solve(dims, planes, flow_axis=1)
+    assert rel(r.g_eff, dims[0] / np.sum(1.0 / t)) < 1e-11
+
+
+def test_stratified_3d_both_directions():
+    """3D layers along z: arithmetic mean along x, harmonic across (z)."""
+    gen = netgen.rng(13)
+    dims = (7, 5, 9)
+    s = np.exp(gen.standard_normal(dims[2]))
+    planes = [np.broadcast_to(s[:, None, None], netgen.plane_shape(dims, 0)).copy(),
+              np.broadcast_to(s[:, None, None], netgen.plane_shape(dims, 1)).copy(),
+              np.broadcast_to(s[:-1, None, None], netgen.plane_shape(dims, 2)).copy()]
+    rx = oracle.solve(dims, planes, flow_axis=0)
+    assert rel(rx.g_eff, dims[1] * s.sum() / (dims[0] - 1)) < 1e-11
+    rz = oracle.solve(dims, planes, flow_axis=2)
+    assert rel(rz.g_eff, dims[0] * dims[1] / np.sum(1.0 / s[:-1])) < 1e-11
+
+
+def test_series_chain():
+    """A single row (ny = 1) is a chain of resistors: G = 1 / sum 1/g."""
+    gen = netgen.rng(14)
+    dims = (40, 1)
+    gx = np.exp(gen.standard_normal((1, 39)))
+    gy = np.zeros((0, 40))
+    r = oracle.solve(dims, [gx, gy])
+    assert rel(r.g_eff, 1.0 / np.sum(1.0 / gx)) < 1e-10
+
+
+# ---------------------------------------------------------------- fixtures
+@pytest.mark.parametrize("name", ["bridge_3x3.txt", "bridge_balanced_3x4.txt"])
+def test_hand_solved_fixture(name):
+    dims, planes, v = ind.read_golden(os.path.join(GOLD, name))
+    r = oracle.solve(dims, planes, flow_axis=int(v["flow_axis"][0]))
+    assert rel(r.g_eff, v["g_eff"][0]) < 1e-13
+    assert rel(r.k_eff, v["k_eff"][0]) < 1e-13
+    np.testing.assert_allclose(r.P, np.array(v["P"]), rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- dense solve
+@pytest.mark.parametrize("dims,f,p", [((6, 5), 0, 1.0), ((5, 7), 1, 1.0), ((4, 3, 5), 2, 1.0),
+                                       ((9, 8), 0, 0.6), ((5, 4, 4), 0, 0.55)])
+def test_dense_direct_solve(dims, f, p):
+    """CG result equals a dense LAPACK solve of the incidence-matrix form."""
+    gen = netgen.rng(100 + len(dims) * 10 + f)
+    planes = netgen.percolate(netgen.loguniform_iid(dims, gen), p, gen)
+    r = oracle.solve(dims, planes, flow_axis=f, p_in=2.0, p_out=0.5)
+    P, qin, qout = ind.dense_solve(dims, planes, f, 2.0, 0.5)
+    np.testing.assert_allclose(r.P.reshape(-1), P, rtol=0, atol=1e-11)
+    assert abs(r.q_in - qin) <= 1e-11 * max(1.0, abs(qin))
+    assert abs(r.q_out - qout) <= 1e-11 * max(1.0, abs(qout))
+
+
+# ---------------------------------------------------------------- labels
+@pytest.mark.parametrize("dims,f,p,seed", [((7, 6), 0, 0.5, 1), ((6, 7), 1, 0.45, 2),
+                                            ((5, 4, 6), 0, 0.3, 3), ((4, 5, 3), 2, 0.35, 4),
+                                            ((10, 10), 0, 0.0, 5), ((10, 10), 0, 1.0, 6)])
+def test_labels_bruteforce_bfs(dims, f, p, seed):
+    gen = netgen.rng(seed)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), p, gen)
+    lab, cls = oracle.labels(dims, planes, flow_axis=f)
+    blab, bcls = ind.bfs_labels(dims, planes, f)
+    np.testing.assert_array_equal(lab.reshape(-1), blab)
+    np.testing.assert_array_equal(cls.reshape(-1), bcls)
+
+
+def test_label_invariants_random():
+    gen = netgen.rng(7)
+    dims = (30, 20)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.5, gen)
+    lab, cls = oracle.labels(dims, planes)
+    lab = lab.reshape(-1)
+    kind = ind.face_kind(dims, 0)
+    for i, j, g in ind.bond_list(dims, planes):
+        if kind[i] or kind[j]:
+            continue
+        if g > 0:
+            assert lab[i] == lab[j]
+    inner = np.where(kind == 0)[0]
+    # label = smallest member
+    for L in np.unique(lab[inner]):
+        members = inner[lab[inner] == L]
+        assert members.min() == L
+
+
+# ---------------------------------------------------------------- invariants
+def _rand_net(seed, dims=(24, 18), p=1.0):
+    gen = netgen.rng(seed)
+    planes = netgen.loguniform_iid(dims, gen)
+    if p < 1.0:
+        planes = netgen.percolate(planes, p, gen)
+    return dims, planes
+
+
+def test_conservation_and_tellegen():
+    """Q_in = Q_out; zero imbalance; Q_in dP = sum_b g dP_b^2 (Tellegen)."""
+    dims, planes = _rand_net(21, p=0.7)
+    r = oracle.solve(dims, planes, p_in=1.0, p_out=0.0)
+    assert r.g_eff > 0
+    assert rel(r.q_out, r.q_in) < 1e-10
+    assert rel(r.energy_g, r.g_eff) < 1e-10
+    imb = oracle.residual(dims, planes, r.P)
+    assert np.max(np.abs(imb)) < 1e-11 * max(1.0, np.max([np.max(g) for g in planes]))
+
+
+def test_rayleigh_bounds():
+    """Cutting transverse bonds lowers G, shorting them raises it."""
+    dims, planes = _rand_net(22, dims=(20, 15))
+    gx = planes[0]
+    r = oracle.solve(dims, planes)
+    g_lo = np.sum(1.0 / np.sum(1.0 / gx, axis=1))
+    g_hi = 1.0 / np.sum(1.0 / np.sum(gx, axis=0))
+    assert g_lo <= r.g_eff * (1 + 1e-12)
+    assert r.g_eff <= g_hi * (1 + 1e-12)
+
+
+def test_scaling_and_bc_affinity():
+    dims, planes = _rand_net(23)
+    r1 = oracle.solve(dims, planes)
+    r2 = oracle.solve(dims, [3.7 * g for g in planes])
+    assert rel(r2.g_eff, 3.7 * r1.g_eff) < 1e-11
+    r3 = oracle.solve(dims, planes, p_in=5.0, p_out=3.0)  # P' = 2 P + 3
+    assert rel(r3.g_eff, r1.g_eff) < 1e-11
+    act = r1.cls == oracle.CLS_SPANNING
+    np.testing.assert_allclose(r3.P[act], 2.0 * r1.P[act] + 3.0, atol=1e-10)
+
+
+def test_mirror_and_transpose_symmetry():
+    dims, planes = _rand_net(24, dims=(14, 11), p=0.8)
+    r = oracle.solve(dims, planes)
+    # mirror along x, faces swap roles: same conductance
+    gm = [planes[0][:, ::-1].copy(), planes[1][:, ::-1].copy()]
+    rm = oracle.solve(dims, gm)
+    assert rel(rm.g_eff, r.g_eff) < 1e-10
+    # transpose: x <-> y with flow along y
+    gt = [planes[1].T.copy(), planes[0].T.copy()]
+    rt = oracle.solve((dims[1], dims[0]), gt, flow_axis=1)
+    assert rel(rt.g_eff, r.g_eff) < 1e-10
+
+
+def test_percolation_no_spanning_cluster():
+    """No open path between the faces: G = 0 exactly."""
+    dims = (12, 9)
+    gen = netgen.rng(25)
+    planes = netgen.lognormal_iid(dims, gen)
+    planes[0][:, 5] = 0.0  # cut every x-bond of column 5 -> 6
+    r = oracle.solve(dims, planes)
+    assert r.g_eff == 0.0 and r.n_active == 0
+    assert r.q_in == 0.0 and r.q_out == 0.0
+
+
+def test_stripping_dead_ends_keeps_g():
+    """Dangling / one-sided clusters carry no current: removing them (zeroing
+    their bonds) does not change G."""
+    dims, planes = _rand_net(26, dims=(16, 16), p=0.6)
+    r = oracle.solve(dims, planes)
+    keep = (r.cls == oracle.CLS_SPANNING) | (r.cls >= oracle.CLS_FACE_IN)
+    kflat = keep.reshape(-1)
+    pruned = [g.copy() for g in planes]
+    for d in range(2):
+        m = list(dims)
+        m[d] -= 1
+        for y in range(m[1]):
+            for x in range(m[0]):
+                i = x + dims[0] * y
+                j = i + (1 if d == 0 else dims[0])
+                if not (kflat[i] and kflat[j]):
+                    pruned[d][y, x] = 0.0
+    rp = oracle.solve(dims, pruned)
+    assert rel(rp.g_eff, r.g_eff) < 1e-10
+
+
+def test_duality_geometric_mean_loose():
+    """2D log-symmetric i.i.d. conductances: G R / S near the geometric mean
+    (Keller-Dykhne duality); statistical, 10 % band."""
+    gen = netgen.rng(27)
+    dims = (96, 96)
+    planes = netgen.lognormal_iid(dims, gen, 1.0)
+    r = oracle.solve(dims, planes, tol=1e-10)
+    assert 0.9 < r.k_eff < 1.1
+
+
+def test_invalid_inputs_rejected():
+    dims = (8, 8)
+    planes = netgen.uniform(dims)
+    bad = [planes[0].copy(), planes[1].copy()]
+    bad[0][2, 3] = -1.0
+    with pytest.raises(ValueError):
+        oracle.solve(dims, bad)
+    bad[0][2, 3] = np.nan
+    with pytest.raises(ValueError):
+        oracle.solve(dims, bad)
+    with pytest.raises(ValueError):
+        oracle.solve((2, 8), netgen.uniform((2, 8)))
