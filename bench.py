@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the Kirchhoff network solve on one GB300 (or N, one per rank).
+
+One step = the whole hot path on one 2048 x 2048 network with long-range
+correlated conductances (FBM, H = 0.7, sigma = 1.5; seeded, synthetic):
+net_create on device-resident bond planes (packing, cluster labelling,
+Jacobi scaling), the mixed-precision solve (FP32 CG inside FP64 iterative
+refinement to a 1e-11 relative residual), and the face flows.  The value is
+solves per second over all ranks (each rank solves its own instance: weak
+scaling, no collective on the data path).  The FP64 CG on the same network is
+timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Solves/s & p99 latency; CG HBM GB/s; mixed vs FP64 CG at 1e-8 rel. conductance"
+WORKLOAD = "2D 2048x2048 bond network, FBM H=0.7 sigma=1.5 conductances, K_x"
+TOL_REL = 1e-11
+L2_FLUSH_BYTES = 512 << 20
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels_cg.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1908_03301_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_hash):
+    """DRAM bytes per inner-iteration launch from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "inner_iter_fbm2048.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def stored_oracle(name):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
+    if not os.path.exists(p):
+        return None
+    return json.load(open(p)).get(name)
+
+
+def oracle_sample(dims, planes, seconds=15.0):
+    """Time the oracle's Jacobi-PCG on the full network for a bounded number of
+    iterations; returns (seconds per iteration, iterations run, threads)."""
+    import oracle
+
+    it = 8
+    t = time.perf_counter()
+    oracle.solve(dims, planes, max_iter=1, tol=0.0)  # set-up cost (labels, diagonal)
+    t_setup = time.perf_counter() - t
+    while True:
+        t = time.perf_counter()
+        oracle.solve(dims, planes, max_iter=it, tol=0.0)
+        dt = time.perf_counter() - t
+        if dt > seconds / 3 or it >= 4096:
+            break
+        it *= 2
+    per_it = max(dt - t_setup, 1e-9) / (it - 1)
+    return per_it, t_setup, it, oracle.max_threads()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    from paper_1908_03301_gb300 import netgen
+
+    dims, planes = netgen.workload_fbm2d(n=a.size)
+    ref = stored_oracle("fbm2048_iso_x") if a.size == 2048 else None
+    iters = ref["iters"] if ref else None
+    step_s = []
+    for k in range(a.warmup + a.steps):
+        per_it, t_setup, it, th = oracle_sample(dims, planes, seconds=6.0)
+        if k >= a.warmup:
+            step_s.append(t_setup + per_it * (iters or 1))
+    mean_s = statistics.mean(step_s)
+    val = 1.0 / mean_s
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": dims[0] * dims[1], "tol_rel": 1e-13,
+                       "solver": "FP64 Jacobi-PCG CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": th, "kind": "oracle",
+                             "sample": f"{it} oracle CG iterations on the full network per step, "
+                                       f"scaled to the {iters} iterations of its full solve "
+                                       f"(stored by tests/golden/make_oracle_reference.py)"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ns.lib(build_if_missing=(world == 1))
+    seed = netgen.SEED_BASE + 1 if rank == 0 else netgen.SEED_BASE + 1000 * 1 + rank
+    dims, planes = netgen.workload_fbm2d(n=a.size, seed=seed)
+    tplanes = [torch.from_numpy(g).to(dev) for g in planes]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(precision):
+        net = ns.Network(dims, tplanes)
+        r = net.solve(ns.make_opts(precision=precision, tol_rel=TOL_REL,
+                                   stream=stream.cuda_stream))
+        q = net.flux()
+        net.close()
+        return r, q
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = []
+        res = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r, q = step(precision)
+            e1.record(stream)
+            evs.append((e0, e1))
+            res.append(r)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return ms, res, wall
+
+    with Clocks(local) as clk:
+        ms, res, wall = timed(ns.NET_MIXED, a.steps, a.warmup)
+    clocks = clk.summary()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * a.steps / (total_ms / 1e3)
+
+    # FP64 CG comparator on the same network
+    ms64, res64, _ = timed(ns.NET_FP64, a.fp64_steps, 1)
+
+    # end to end through the public API from pinned host memory
+    pinned = [torch.from_numpy(g).pin_memory() for g in planes]
+    hplanes = [p.numpy() for p in pinned]
+    N = dims[0] * dims[1]
+    Pout = torch.empty(N, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(1 + a.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        net = ns.Network(dims, hplanes)
+        r = net.solve(ns.make_opts(tol_rel=TOL_REL))
+        lib = ns.lib()
+        st = lib.net_get_pressure(net.h, Pout.data_ptr(), N, 0)
+        net.close()
+        dt = time.perf_counter() - t
+        assert st == 0
+        if k > 0:
+            e2e_t.append(dt)
+    h2d = sum(g.nbytes for g in planes)
+    d2h = N * 8 + 64
+
+    if rank != 0:
+        return
+    r0 = res[-1]
+    d = len(dims)
+    b_alg = 32 + 4 * d  # bytes per active unknown per FP32 inner iteration
+    inner_s = r0.inner_ms / 1e3
+    achieved = b_alg * r0.n_active * r0.inner_iters / inner_s / 1e9 if inner_s > 0 else None
+    peaks_p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_p):
+        peak, peak_src = float(json.load(open(peaks_p))["hbm_gbs"]), "measured"
+    khash = kernel_source_hash()
+    traffic = profiled_traffic(khash)
+    ref = stored_oracle("fbm2048_iso_x") if a.size == 2048 else None
+    rel_vs_oracle = abs(r0.g_eff - ref["g_eff"]) / ref["g_eff"] if ref else None
+    rel64 = abs(res64[-1].g_eff - ref["g_eff"]) / ref["g_eff"] if ref else None
+    launches_setup = d + 5 + 1 + 1
+    launches = launches_setup + 1 + (1 + r0.outer_iters) + r0.inner_launches
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "n_active": r0.n_active,
+                   "precision": "FP32 inner CG / FP64 refinement", "tol_rel": TOL_REL,
+                   "l2": "flushed between steps (512 MiB write)"},
+        "p50_ms": statistics.median(ms),
+        "p99_ms": float(np.percentile(ms, 99)),
+        "wall_s": wall,
+        "accuracy": {"g_eff": r0.g_eff, "rel_err_vs_oracle": rel_vs_oracle,
+                     "rel_residual": r0.rel_residual, "max_imbalance": r0.max_imbalance,
+                     "outer_iters": r0.outer_iters, "inner_iters": r0.inner_iters,
+                     "fp64_fallback": r0.fp64_fallback},
+        "fp64_cg": {"value": a.fp64_steps / (sum(ms64) / 1e3), "unit": "solves/s",
+                    "ms_per_step": statistics.mean(ms64), "inner_iters": res64[-1].inner_iters,
+                    "rel_err_vs_oracle": rel64,
+                    "speedup_mixed_over_fp64": statistics.mean(ms64) / statistics.mean(ms)},
+        "cg_hbm_gbs": achieved,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "inner_iter_kernel<float,2>", "peak_source": peak_src,
+                     "bytes_per_unknown_iter": b_alg},
+        "e2e": {"value": len(e2e_t) / sum(e2e_t), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches * a.steps),
+        "clocks": clocks,
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        it_full = ref["iters"] if ref else None
+        per_it, t_setup, it, th = oracle_sample(dims, planes, seconds=15.0)
+        if it_full:
+            v = 1.0 / (t_setup + per_it * it_full)
+            sample = (f"{it} oracle CG iterations on the full 2048^2 network, scaled to the "
+                      f"{it_full} iterations of its full solve")
+            line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": th, "kind": "oracle",
+                                    "sample": sample}
+        else:
+            line["cpu_baseline"] = {"value": 1.0 / per_it / 1.0, "unit": "CG iterations/s",
+                                    "cores": th, "kind": "oracle",
+                                    "sample": f"{it} oracle CG iterations on the full network"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_ours(a, rank, world, local)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * netsolve.h -- C ABI of the GB300 Kirchhoff network solver.
+ *
+ * The solver computes the steady flow through a 2D square or 3D cubic bond
+ * network (pore network / random-resistor network) with one conductance per
+ * bond, following Dashtian & Sahimi, arXiv:1908.03301:
+ *
+ *   Sec. II   each bond ij carries q_ij = g_ij (P_j - P_i);
+ *   Eq. 3     mass balance sum_j q_ij = 0 at every interior node: G P = b;
+ *   Sec. II   a fixed pressure drop along one axis: the face x_f = 0 is held
+ *             at p_in and the face x_f = n_f - 1 at p_out (here the transverse
+ *             boundaries are no-flow);
+ *   Eq. 4     K = (Q / S)(mu L / dP), with Q the total flow through the inlet
+ *             face, L = n_f - 1, S = product of the transverse node counts
+ *             and mu = 1 (lattice units);
+ *   Sec. IV   G P = b solved by conjugate gradients with single-precision
+ *             inner iterations inside a double-precision iterative
+ *             refinement loop.
+ *
+ * Before the solve every network is split into clusters of nodes joined by
+ * open bonds (g > 0).  Only clusters with open bonds to both faces carry
+ * flow; the others are removed from the linear system (their pressure is
+ * p_in for clusters touching only the inlet, p_out for clusters touching
+ * only the outlet, 0 for isolated ones).  Labels are canonical: the smallest
+ * linear node index of the cluster, -1 on the inlet face, -2 on the outlet.
+ *
+ * Layout of every node array: node (x, y, z) has linear index
+ * x + nx * (y + ny * z), x fastest.  Bond plane d (0 = x, 1 = y, 2 = z) holds
+ * the bond from node c to node c + e_d; its extents are the node extents with
+ * n_d reduced by one, indexed the same way (x fastest).  A plane of extent 0
+ * (e.g. ny = 1) may be NULL.
+ *
+ * Errors: every call returns a net_status; nothing aborts or throws across
+ * this boundary.  net_last_error() gives a thread-local message for the last
+ * failing call on the calling thread.  Any call accepts a NULL handle and
+ * returns NET_EINVAL.
+ *
+ * Threads: a net_t may be used by one thread at a time.  A netq_t may be used
+ * from any number of threads.
+ *
+ * Device: the library runs on the CUDA device that is current on the calling
+ * thread at net_create / netq_create time and keeps all state resident there.
+ */
+#ifndef NETSOLVE_H
+#define NETSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct net_s net_t;    /* one resident network (opaque) */
+typedef struct netq_s netq_t;  /* a continuous-batching request queue (opaque) */
+
+typedef enum {
+    NET_OK = 0,
+    NET_EINVAL = 1,         /* bad argument or bad network (see net_create) */
+    NET_ENOMEM = 2,         /* device or host allocation failed */
+    NET_EBUDGET = 3,        /* request larger than the queue's memory budget */
+    NET_ENOTCONVERGED = 4,  /* iteration caps reached above the tolerance */
+    NET_ETIMEOUT = 5,       /* a bounded wait gave up (device or host) */
+    NET_ECUDA = 6,          /* a CUDA runtime call failed */
+    NET_ECANCELLED = 7,     /* request cancelled / queue shut down */
+    NET_EBUSY = 8           /* result not ready yet (netq_poll) */
+} net_status;
+
+enum { NET_F64 = 0, NET_F32 = 1 };      /* bond conductance dtype */
+enum { NET_MIXED = 0, NET_FP64 = 1 };   /* solver precision */
+
+/* Cluster classes returned by net_get_labels. */
+enum {
+    NET_CLS_ISOLATED = 0,  /* no open bond to either face: P = 0 */
+    NET_CLS_INLET = 1,     /* open bonds to the inlet face only: P = p_in */
+    NET_CLS_OUTLET = 2,    /* open bonds to the outlet face only: P = p_out */
+    NET_CLS_SPANNING = 3,  /* open bonds to both faces: solved */
+    NET_CLS_FACE_IN = 4,   /* node on the inlet face (fixed p_in) */
+    NET_CLS_FACE_OUT = 5   /* node on the outlet face (fixed p_out) */
+};
+
+/* Network description (Sec. II; boundary conditions as stated above). */
+typedef struct {
+    int ndim;                /* 2 or 3 */
+    int64_t n[3];            /* node extents (nx, ny, nz); n[2] = 1 in 2D */
+    int flow_axis;           /* axis of the pressure drop, 0 <= flow_axis < ndim;
+                                n[flow_axis] >= 3 */
+    unsigned periodic_mask;  /* must be 0 (no-flow transverse boundaries) */
+    double p_in, p_out;      /* face pressures, finite, p_in != p_out */
+    int bond_dtype;          /* NET_F64 or NET_F32 */
+    int on_device;           /* 1: bond pointers are device pointers on the
+                                current device; 0: host pointers */
+    void *stream;            /* cudaStream_t for set-up work; NULL = the
+                                library's own stream for this network */
+} net_desc;
+
+/* Solver options.  net_opts_default() fills the defaults listed here. */
+typedef struct {
+    int precision;           /* NET_MIXED (default) or NET_FP64 */
+    double tol_rel;          /* outer stop: ||b - G P||_2 <= tol_rel ||b||_2;
+                                default 1e-11 */
+    double tol_inner;        /* inner relative reduction per refinement step
+                                (mixed); default 1e-4 */
+    int max_outer;           /* refinement steps; default 40 */
+    int64_t max_inner;       /* CG iterations per inner solve; default 200000 */
+    int check_every;         /* inner iterations per device-flag check;
+                                0 = choose automatically */
+    const double *x0;        /* optional initial pressures (N doubles, node
+                                layout; entries on faces are ignored); NULL =
+                                linear profile along the flow axis */
+    int x0_on_device;        /* x0 is a device pointer */
+    void *stream;            /* cudaStream_t to run on; NULL = network's own */
+} net_opts;
+
+/* Per-solve result and diagnostics. */
+typedef struct {
+    double g_eff;            /* effective conductance Q_in / (p_in - p_out) */
+    double k_eff;            /* Eq. 4: g_eff * (n_f - 1) / S */
+    double q_in, q_out;      /* total flow through the inlet / outlet face */
+    double rel_residual;     /* ||b - G P||_2 / ||b||_2, FP64 true residual */
+    double max_imbalance;    /* max nodal current imbalance |b - G P|_inf */
+    double energy_g;         /* sum_bonds g dP_b^2 / (p_in - p_out)^2 */
+    int64_t n_active;        /* unknowns in spanning clusters */
+    int outer_iters;         /* refinement steps taken */
+    int64_t inner_iters;     /* CG iterations summed over refinement steps */
+    int fp64_fallback;       /* 1 if the inner solve was switched to FP64 */
+    float ms;                /* wall time of the solve on its stream */
+    float inner_ms;          /* device time spent in the inner CG loop */
+    int64_t inner_launches;  /* inner CG kernel launches (incl. no-op tails) */
+    net_status status;
+} net_result;
+
+/* Fill *opts with the defaults listed in net_opts. */
+void net_opts_default(net_opts *opts);
+
+/*
+ * Create a network: copy the bond planes to the device, label clusters,
+ * build the scaled system (diagonal, right-hand side, initial pressures).
+ *   desc   network description (read during the call only).
+ *   g[d]   bond plane d for d < ndim, dtype desc->bond_dtype, host or device
+ *          per desc->on_device; copied, the caller keeps ownership.  Planes
+ *          with zero entries may be NULL.
+ *   out    receives the handle; the library owns its device state until
+ *          net_destroy.
+ * Errors: NET_EINVAL for ndim not 2/3, an extent < 1, n_f < 3, more than
+ * 2^31 - 1 padded nodes, periodic_mask != 0, non-finite or equal pressures,
+ * or a conductance that is negative, NaN or infinite (checked on the
+ * device); NET_ENOMEM / NET_ECUDA otherwise.  A network without a spanning
+ * cluster is valid and solves to g_eff = 0.  The call returns after the
+ * set-up work has completed on the device.
+ */
+net_status net_create(const net_desc *desc, const void *const g[3], net_t **out);
+
+/*
+ * Solve Eq. 3 for the network (Sec. IV: CG, single-precision inner loop in a
+ * double-precision refinement loop; NET_FP64 runs the inner loop in FP64).
+ * The preconditioner is Jacobi, applied as the symmetric scaling
+ * D^-1/2 G D^-1/2.  Pressures stay on the device (net_get_pressure).
+ *   opts   NULL = defaults.   out   receives the result (required).
+ * Returns out->status: NET_OK, NET_ENOTCONVERGED (caps reached; the result
+ * holds the best pressures reached), NET_ECUDA, NET_EINVAL.
+ */
+net_status net_solve(net_t *net, const net_opts *opts, net_result *out);
+
+/*
+ * Flows of the last solve (Eq. 4): total flow into the inlet face, out of the
+ * outlet face, and the effective conductance q_in / (p_in - p_out).  Any
+ * output pointer may be NULL.  NET_EINVAL before the first solve.
+ */
+net_status net_flux(net_t *net, double *q_in, double *q_out, double *g_eff);
+
+/*
+ * Copy the N = nx*ny*nz node pressures (FP64, node layout) to dst, a host or
+ * device buffer of at least n doubles (n >= N, else NET_EINVAL).  Face nodes
+ * hold p_in / p_out; removed clusters hold their fixed pressure.
+ */
+net_status net_get_pressure(net_t *net, double *dst, int64_t n, int dst_on_device);
+
+/*
+ * Copy the cluster labels (int32) and classes (uint8, NET_CLS_*) of the N
+ * nodes into host buffers of at least n entries.  Either pointer may be NULL.
+ */
+net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int64_t n);
+
+/* Release the network's device state.  NULL is accepted. */
+net_status net_destroy(net_t *net);
+
+/* Thread-local message describing the last failing call on this thread. */
+const char *net_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,182 @@
+// common.cuh -- shared device-side definitions of the network solver.
+//
+// Internal layout ("padded grid"): node (x, y, z) lives at
+//     idx = pad + x + px * (y + ny * z),   px = round_up(nx, 4),
+// so every row starts on a 16-byte boundary for both float and double.
+// Columns x in [nx, px) are ghost nodes: zero conductance, zero vectors.
+// `pad` zero elements precede and follow the grid (pad >= the largest
+// neighbour offset), so the stencil never indexes outside an allocation.
+// Bond plane d over the padded grid holds at idx(c) the conductance of the
+// bond c -> c + e_d, and 0 where that bond does not exist.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace netsolve {
+
+struct Geom {
+    int ndim;        // 2 or 3
+    int f;           // flow axis
+    int nx, ny, nz;  // node extents (nz = 1 in 2D)
+    int px;          // row pitch
+    int nf;          // extent along the flow axis
+    long long plane; // px * ny
+    long long pad;   // zero elements before (and after) the grid
+    long long len;   // pad + plane * nz + pad
+    double p_in, p_out;
+
+    __host__ __device__ long long idx(int x, int y, int z) const {
+        return pad + x + (long long)px * (y + (long long)ny * z);
+    }
+    __host__ __device__ long long stride(int d) const {
+        return d == 0 ? 1 : (d == 1 ? (long long)px : plane);
+    }
+    __host__ __device__ int coord(int d, int x, int y, int z) const {
+        return d == 0 ? x : (d == 1 ? y : z);
+    }
+    __host__ __device__ int extent(int d) const {
+        return d == 0 ? nx : (d == 1 ? ny : nz);
+    }
+};
+
+// Cluster classes (same values as the NET_CLS_* constants of the C ABI).
+enum : uint8_t {
+    CLS_ISOLATED = 0, CLS_INLET = 1, CLS_OUTLET = 2, CLS_SPANNING = 3,
+    CLS_FACE_IN = 4, CLS_FACE_OUT = 5, CLS_GHOST = 255
+};
+
+// Scalars of one inner CG solve, in device memory.  The fused iteration
+// kernel reads alpha/beta/iter/stop at entry; the last CTA to finish writes
+// the next values, after every other CTA has read them.
+struct InnerScal {
+    double alpha, beta;   // step lengths for the next iteration
+    double rho0;          // ||r_0||^2 of this inner solve
+    double tol2;          // stop when ||r||^2 <= tol2 * rho0
+    double rho;           // last directly computed ||r||^2
+    double best;          // smallest ||r||^2 seen (stagnation watch)
+    long long best_iter;
+    long long iter;       // iteration kernels that did work in this solve
+    long long max_iter;
+    long long stag_window;
+    int stop;             // 0 run, 1 converged, 2 cap, 3 stagnated, 4 breakdown
+    unsigned int counter; // CTA arrival counter of the running launch
+};
+
+// Sums of one outer (FP64) residual pass.
+struct OuterScal {
+    double rr;       // sum r_i^2 over interior nodes
+    double rmax;     // max |r_i|
+    double rh2;      // sum (D^-1/2 r)_i^2
+    double qin, qout, energy;
+    unsigned int counter;
+};
+
+// Sums of the set-up pass.
+struct SetupScal {
+    double bb;             // ||b||^2
+    unsigned long long n_active;
+    unsigned int counter;
+    unsigned int bad;      // nonzero: a conductance was negative / NaN / inf
+};
+
+// ---------------------------------------------------------------------------
+// deterministic reductions
+// ---------------------------------------------------------------------------
+enum { RED_SUM = 0, RED_MAX = 1 };
+
+template <int OP>
+__device__ __forceinline__ double red_op(double a, double b) {
+    return OP == RED_SUM ? a + b : fmax(a, b);
+}
+
+// Block-wide reduction of NV values; every thread receives the result.
+// Order is fixed by thread index, so the result is reproducible.
+template <int NV, int NT>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], const int (&ops)[NV]) {
+    __shared__ double s_red[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = ops[k] == RED_SUM ? v[k] + t : fmax(v[k], t);
+        }
+    }
+    __syncthreads();  // s_red may still be read from a previous call
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) s_red[warp][k] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double a = s_red[0][k];
+        for (int w = 1; w < NT / 32; w++) a = ops[k] == RED_SUM ? a + s_red[w][k] : fmax(a, s_red[w][k]);
+        v[k] = a;
+    }
+}
+
+// Grid-wide reduction through per-CTA partials and an arrival counter: the
+// last CTA to arrive sums the partials in CTA order and returns true with
+// the totals in v (all its threads).  Other CTAs return false.  The counter
+// is reset by the last CTA so the same storage serves the next launch.
+template <int NV, int NT>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], const int (&ops)[NV],
+                                            double *partials, unsigned int *counter) {
+    __shared__ bool s_last;
+    block_reduce<NV, NT>(v, ops);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) partials[(long long)b * NV + k] = v[k];
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        s_last = (t == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = ops[k] == RED_SUM ? 0.0 : -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += NT) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double p = __ldcg(&partials[(long long)i * NV + k]);
+            v[k] = ops[k] == RED_SUM ? v[k] + p : fmax(v[k], p);
+        }
+    }
+    block_reduce<NV, NT>(v, ops);
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// 16-byte vector of T (float4 / double2) with element access.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    static constexpr int N = 4;
+    float v[4];
+    __device__ __forceinline__ void load(const float *p) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ void store(float *p) const {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.f; }
+};
+template <> struct Vec<double> {
+    static constexpr int N = 2;
+    double v[2];
+    __device__ __forceinline__ void load(const double *p) {
+        double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ __forceinline__ void store(double *p) const {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+    __device__ __forceinline__ void zero() { v[0] = v[1] = 0.0; }
+};
+
+}  // namespace netsolve

@@ -1,0 +1,70 @@
+// kernels.h -- host-side launchers of the solver kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace netsolve {
+
+// ---- set-up (kernels_setup.cu) --------------------------------------------
+// Copy user bond plane d (compact layout, dtype src_f32 ? float : double,
+// device memory) into the padded plane dst (dtype dst_f32 ? float : double);
+// sets *bad if a value is negative, NaN or infinite.
+cudaError_t launch_pack_bonds(const Geom &g, int d, const void *src, int src_f32, void *dst,
+                              int dst_f32, unsigned int *bad, cudaStream_t st);
+// Cluster labelling (union-find, min-index roots) and classes.
+cudaError_t launch_labels(const Geom &g, const void *const graw[3], int f32, int *parent,
+                          unsigned int *flags, uint8_t *cls, cudaStream_t st);
+// Diagonal scaling, initial pressures, ||b||^2 and the active count.
+cudaError_t launch_build_system(const Geom &g, const void *const graw[3], int f32,
+                                const uint8_t *cls, double *dis, double *x, SetupScal *ss,
+                                double *partials, cudaStream_t st);
+// Scaled bonds ghat_d = g_d D_i^-1/2 D_j^-1/2 (0 unless both ends are solved).
+cudaError_t launch_build_scaled(const Geom &g, const void *const graw[3], int f32,
+                                const double *dis, void *const gs[3], int gs_f32,
+                                cudaStream_t st);
+// Overwrite solved pressures with a caller's initial guess (compact, device).
+cudaError_t launch_apply_x0(const Geom &g, const uint8_t *cls, const double *x0c, double *x,
+                            cudaStream_t st);
+// Padded -> compact copies for output.
+cudaError_t launch_unpack_x(const Geom &g, const double *x, double *dst, cudaStream_t st);
+cudaError_t launch_unpack_labels(const Geom &g, const int *parent, const uint8_t *cls,
+                                 int *label, uint8_t *cls_out, cudaStream_t st);
+
+// ---- solve (kernels_cg.cu) -------------------------------------------------
+struct InnerArgs {
+    Geom g;
+    const void *gs[3];  // scaled bonds (T)
+    void *y;              // inner solution (T)
+    void *r[2], *p[2], *q[2];  // double-buffered inner vectors (T)
+    InnerScal *s;
+    double *partials;
+};
+// Number of CTAs the inner iteration kernel uses for this geometry.
+int inner_grid_blocks(const Geom &g, int f32);
+cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st);
+
+struct OuterArgs {
+    Geom g;
+    const void *graw[3];  // raw bonds (double or float)
+    int raw_f32;
+    const double *dis;
+    double *x;
+    const void *y;        // inner correction (T), read when apply_corr
+    void *r_out;          // scaled residual for the next inner solve (T):
+                          // buffer r[0] of the inner vectors
+    int inner_f32;
+    int apply_corr;       // first apply x += D^-1/2 y (separate kernel)
+    int corr_f32;         // dtype of y
+    OuterScal *os;
+    InnerScal *is;        // inner scalars to arm for the next inner solve
+    double tol_floor;     // smallest relative reduction asked of the inner solve
+    double tol_rel;       // outer tolerance (relative 2-norm residual)
+    double bnorm;         // ||b||_2
+    long long max_inner, stag_window;
+    double *partials;
+};
+int outer_grid_blocks(const Geom &g);
+cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st);
+
+}  // namespace netsolve

@@ -1,0 +1,557 @@
+// runtime.cu -- the C ABI of include/netsolve.h: network set-up, the
+// iterative-refinement driver around the CG kernels, result read-back.
+//
+// Iterative refinement (Sec. IV, "mixed-precision method"): the FP64 outer
+// loop recomputes the true residual r = b - G x on the device, the inner CG
+// solves D^-1/2 G D^-1/2 y = D^-1/2 r in FP32 to a relative reduction
+// tol_inner, and the outer pass applies x += D^-1/2 y.  The inner iterations
+// run as CUDA-graph chunks of `check_every` fused iteration kernels; the host
+// reads one device flag per chunk.  Nothing is summed on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/netsolve.h"
+#include "kernels.h"
+#include "runtime_internal.h"
+
+using namespace netsolve;
+
+namespace {
+thread_local std::string g_err;
+}
+
+namespace netsolve {
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+net_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return NET_ECUDA;
+}
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+net_status make_geom(const net_desc *d, Geom *g) {
+    if (!d) { set_error("desc is NULL"); return NET_EINVAL; }
+    if (d->ndim != 2 && d->ndim != 3) { set_error("ndim must be 2 or 3"); return NET_EINVAL; }
+    for (int a = 0; a < 3; a++)
+        if (d->n[a] < 1 || d->n[a] > (1LL << 30)) { set_error("extent n[%d] out of range", a); return NET_EINVAL; }
+    if (d->ndim == 2 && d->n[2] != 1) { set_error("2D network needs n[2] == 1"); return NET_EINVAL; }
+    if (d->flow_axis < 0 || d->flow_axis >= d->ndim) { set_error("flow_axis out of range"); return NET_EINVAL; }
+    if (d->n[d->flow_axis] < 3) { set_error("need at least 3 nodes along the flow axis"); return NET_EINVAL; }
+    if (d->periodic_mask != 0) { set_error("periodic boundaries are not supported"); return NET_EINVAL; }
+    if (!std::isfinite(d->p_in) || !std::isfinite(d->p_out) || d->p_in == d->p_out) {
+        set_error("face pressures must be finite and differ");
+        return NET_EINVAL;
+    }
+    if (d->bond_dtype != NET_F64 && d->bond_dtype != NET_F32) { set_error("bad bond_dtype"); return NET_EINVAL; }
+    Geom G{};
+    G.ndim = d->ndim;
+    G.f = d->flow_axis;
+    G.nx = (int)d->n[0];
+    G.ny = (int)d->n[1];
+    G.nz = (int)d->n[2];
+    G.px = (int)round_up(G.nx, 4);
+    G.nf = (int)d->n[d->flow_axis];
+    G.plane = (long long)G.px * G.ny;
+    G.pad = round_up(d->ndim == 3 ? G.plane : (long long)G.px, 64);
+    G.len = G.pad + G.plane * G.nz + G.pad;
+    G.p_in = d->p_in;
+    G.p_out = d->p_out;
+    if (G.len >= (1LL << 31)) { set_error("network too large (padded nodes >= 2^31)"); return NET_EINVAL; }
+    *g = G;
+    return NET_OK;
+}
+
+long long plane_elems(const Geom &g, int d) {
+    long long m[3] = {g.nx, g.ny, g.nz};
+    m[d] -= 1;
+    return m[0] * m[1] * m[2];
+}
+
+size_t net_footprint_bytes(const Geom &g, int raw_f32) {
+    const size_t L = (size_t)g.len, nd = (size_t)g.ndim;
+    size_t b = nd * L * (raw_f32 ? 4 : 8);  // raw bonds
+    b += L * (4 + 1 + 8 + 8);                // parent, cls, dis, x
+    b += nd * L * 4;                         // scaled FP32 bonds
+    b += 7 * L * 4;                          // FP32 inner vectors
+    b += L * 4;                              // label flags (set-up only)
+    return b;
+}
+
+}  // namespace netsolve
+
+// ---------------------------------------------------------------------------
+namespace {
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) return e;
+    *p = (T *)q;
+    return cudaMemsetAsync(q, 0, bytes ? bytes : 16, st);
+}
+
+void dfree(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+net_status ensure_precision(net_t *n, int f32) {
+    const int k = f32 ? 0 : 1;
+    cudaStream_t st = n->stream;
+    const size_t L = (size_t)n->g.len;
+    const size_t es = f32 ? 4 : 8;
+    if (!n->gs[k][0]) {
+        for (int d = 0; d < n->g.ndim; d++) CK(dalloc(&n->gs[k][d], L * es, st));
+        void *gs3[3] = {n->gs[k][0], n->gs[k][1], n->gs[k][2]};
+        const void *gr[3] = {n->graw[0], n->graw[1], n->graw[2]};
+        CK(launch_build_scaled(n->g, gr, n->raw_f32, n->dis, gs3, f32, st));
+    }
+    if (!n->vec[k]) CK(dalloc(&n->vec[k], 7 * L * es, st));
+    return NET_OK;
+}
+
+net_status ensure_graph(net_t *n, int f32, int K) {
+    const int k = f32 ? 0 : 1;
+    if (n->gexec[k] && n->gk[k] == K) return NET_OK;
+    if (n->gexec[k]) {
+        cudaGraphExecDestroy(n->gexec[k]);
+        n->gexec[k] = nullptr;
+    }
+    InnerArgs a = inner_args(n, f32);
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int i = 0; e == cudaSuccess && i < K; i++) e = launch_inner_iter(a, f32, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&n->gexec[k], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "inner graph");
+    n->gk[k] = K;
+    return NET_OK;
+}
+
+}  // namespace
+
+namespace netsolve {
+
+InnerArgs inner_args(net_t *n, int f32) {
+    const int k = f32 ? 0 : 1;
+    const size_t L = (size_t)n->g.len, es = f32 ? 4 : 8;
+    char *v = (char *)n->vec[k];
+    InnerArgs a{};
+    a.g = n->g;
+    for (int d = 0; d < 3; d++) a.gs[d] = n->gs[k][d] ? n->gs[k][d] : n->gs[k][0];
+    a.y = v;
+    a.r[0] = v + 1 * L * es;
+    a.r[1] = v + 2 * L * es;
+    a.p[0] = v + 3 * L * es;
+    a.p[1] = v + 4 * L * es;
+    a.q[0] = v + 5 * L * es;
+    a.q[1] = v + 6 * L * es;
+    a.s = &n->dsc->in[k];
+    a.partials = n->partials;
+    return a;
+}
+
+OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op) {
+    const int k = f32 ? 0 : 1, kc = corr_f32 ? 0 : 1;
+    OuterArgs o{};
+    o.g = n->g;
+    for (int d = 0; d < 3; d++) o.graw[d] = n->graw[d] ? n->graw[d] : n->graw[0];
+    o.raw_f32 = n->raw_f32;
+    o.dis = n->dis;
+    o.x = n->x;
+    // the correction comes from the inner precision used last
+    o.y = n->vec[kc];
+    o.apply_corr = apply_corr && n->vec[kc] != nullptr;
+    o.corr_f32 = corr_f32;
+    const size_t es = f32 ? 4 : 8;
+    o.r_out = (char *)n->vec[k] + 1 * (size_t)n->g.len * es;
+    o.inner_f32 = f32;
+    o.os = &n->dsc->os;
+    o.is = &n->dsc->in[k];
+    o.tol_floor = f32 ? op.tol_inner : 0.0;
+    o.tol_rel = op.tol_rel;
+    o.bnorm = n->bnorm;
+    o.max_inner = op.max_inner;
+    o.stag_window = std::max(400LL, 8LL * std::max(n->g.nx, std::max(n->g.ny, n->g.nz)));
+    o.partials = n->partials;
+    return o;
+}
+
+// Outer correction with y of one precision but the residual written for
+// another needs both inner buffers; outer_kernel reads y as the *target*
+// precision's type, so a switch of precision first re-arms with no correction
+// pending (see solve_impl).
+
+net_status setup_network(net_t *n, const void *const g[3], int on_device) {
+    cudaStream_t st = n->stream;
+    const Geom &G = n->g;
+    const size_t L = (size_t)G.len, rs = n->raw_f32 ? 4 : 8;
+    for (int d = 0; d < G.ndim; d++) CK(dalloc(&n->graw[d], L * rs, st));
+    CK(dalloc(&n->parent, L * 4, st));
+    CK(dalloc(&n->cls, L, st));
+    CK(dalloc(&n->dis, L * 8, st));
+    CK(dalloc(&n->x, L * 8, st));
+    const long long nb = std::max<long long>(
+        {(long long)inner_grid_blocks(G, 1), (long long)inner_grid_blocks(G, 0),
+         (long long)outer_grid_blocks(G), 152LL * 16});
+    CK(dalloc(&n->partials, (size_t)nb * 8 * sizeof(double), st));
+    CK(dalloc(&n->dsc, sizeof(DevScal), st));
+    unsigned int *flags = nullptr;
+    CK(dalloc(&flags, L * 4, st));
+    void *stage = nullptr;
+    for (int d = 0; d < G.ndim; d++) {
+        const long long m = plane_elems(G, d);
+        if (m == 0) continue;  // plane of extent 0: nothing to copy
+        if (!g || !g[d]) { dfree(flags, st); set_error("bond plane %d is NULL", d); return NET_EINVAL; }
+        const void *src = g[d];
+        if (!on_device) {
+            if (!stage) CK(dalloc(&stage, (size_t)std::max({plane_elems(G, 0), plane_elems(G, 1),
+                                                           G.ndim == 3 ? plane_elems(G, 2) : 0LL}) * rs, st));
+            CK(cudaMemcpyAsync(stage, g[d], (size_t)m * rs, cudaMemcpyHostToDevice, st));
+            src = stage;
+        }
+        CK(launch_pack_bonds(G, d, src, n->raw_f32, n->graw[d], n->raw_f32, &n->dsc->ss.bad, st));
+    }
+    const void *gr[3] = {n->graw[0], n->graw[1], G.ndim == 3 ? n->graw[2] : n->graw[0]};
+    CK(launch_labels(G, gr, n->raw_f32, n->parent, flags, n->cls, st));
+    CK(launch_build_system(G, gr, n->raw_f32, n->cls, n->dis, n->x, &n->dsc->ss, n->partials, st));
+    dfree(flags, st);
+    dfree(stage, st);
+    CK(cudaMemcpyAsync(n->hsc, n->dsc, sizeof(DevScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n->hsc->ss.bad) {
+        set_error("a conductance is negative, NaN or infinite");
+        return NET_EINVAL;
+    }
+    n->bnorm = std::sqrt(n->hsc->ss.bb);
+    n->n_active = (long long)n->hsc->ss.n_active;
+    return NET_OK;
+}
+
+void release_network(net_t *n) {
+    if (!n) return;
+    cudaStream_t st = n->stream;
+    for (int k = 0; k < 2; k++) {
+        if (n->gexec[k]) cudaGraphExecDestroy(n->gexec[k]);
+        for (int d = 0; d < 3; d++) dfree(n->gs[k][d], st);
+        dfree(n->vec[k], st);
+    }
+    for (int d = 0; d < 3; d++) dfree(n->graw[d], st);
+    dfree(n->parent, st);
+    dfree(n->cls, st);
+    dfree(n->dis, st);
+    dfree(n->x, st);
+    dfree(n->partials, st);
+    dfree(n->dsc, st);
+    cudaStreamSynchronize(st);
+    if (n->hsc) cudaFreeHost(n->hsc);
+    if (n->ev[0]) for (int i = 0; i < 4; i++) cudaEventDestroy(n->ev[i]);
+    if (n->own_stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+net_status create_network(const net_desc *desc, const void *const g[3], net_t **out) {
+    if (!out) { set_error("out is NULL"); return NET_EINVAL; }
+    *out = nullptr;
+    Geom G;
+    net_status s = make_geom(desc, &G);
+    if (s != NET_OK) return s;
+    net_t *n = new net_t();
+    n->g = G;
+    n->raw_f32 = desc->bond_dtype == NET_F32;
+    cudaGetDevice(&n->device);
+    cudaError_t e;
+    if (desc->stream) {
+        n->stream = (cudaStream_t)desc->stream;
+        n->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete n; return cuda_fail(e, "stream"); }
+        n->own_stream = true;
+    }
+    e = cudaMallocHost(&n->hsc, sizeof(DevScal));
+    if (e == cudaSuccess)
+        for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&n->ev[i]);
+    if (e != cudaSuccess) { release_network(n); return cuda_fail(e, "host state"); }
+    s = setup_network(n, g, desc->on_device);
+    if (s != NET_OK) {
+        std::string keep = g_err;
+        release_network(n);
+        g_err = keep;
+        return s;
+    }
+    *out = n;
+    return NET_OK;
+}
+
+// One solve.  Returns the status and fills *r.
+net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
+    net_opts o;
+    net_opts_default(&o);
+    if (o_in) o = *o_in;
+    memset(r, 0, sizeof(*r));
+    if (o.precision != NET_MIXED && o.precision != NET_FP64) { set_error("bad precision"); return r->status = NET_EINVAL; }
+    if (!(o.tol_rel > 0.0) || !(o.tol_inner > 0.0) || o.max_outer < 1 || o.max_inner < 1) {
+        set_error("bad tolerances or caps");
+        return r->status = NET_EINVAL;
+    }
+    cudaStream_t st = o.stream ? (cudaStream_t)o.stream : n->stream;
+    const Geom &G = n->g;
+    const double dP = G.p_in - G.p_out;
+    int f32 = o.precision == NET_MIXED;
+    const int K = o.check_every > 0 ? o.check_every : 32;
+    if (st != n->stream) {
+        // make the caller's stream wait for the network's set-up work
+        CK(cudaEventRecord(n->ev[3], n->stream));
+        CK(cudaStreamWaitEvent(st, n->ev[3], 0));
+    }
+    net_status s = ensure_precision(n, f32);
+    if (s != NET_OK) return r->status = s;
+    s = ensure_graph(n, f32, K);
+    if (s != NET_OK) return r->status = s;
+
+    CK(cudaEventRecord(n->ev[0], st));
+    // fresh start: initial pressures, then the caller's guess
+    {
+        const void *gr[3] = {n->graw[0], n->graw[1], G.ndim == 3 ? n->graw[2] : n->graw[0]};
+        CK(launch_build_system(G, gr, n->raw_f32, n->cls, n->dis, n->x, &n->dsc->ss, n->partials, st));
+        if (o.x0) {
+            const double *x0d = o.x0;
+            double *tmp = nullptr;
+            const size_t nb = sizeof(double) * (size_t)G.nx * G.ny * G.nz;
+            if (!o.x0_on_device) {
+                CK(dalloc(&tmp, nb, st));
+                CK(cudaMemcpyAsync(tmp, o.x0, nb, cudaMemcpyHostToDevice, st));
+                x0d = tmp;
+            }
+            CK(launch_apply_x0(G, n->cls, x0d, n->x, st));
+            dfree(tmp, st);
+        }
+    }
+    // first residual pass (no correction pending)
+    OuterArgs oa = outer_args(n, f32, 0, f32, o);
+    CK(launch_outer(oa, st));
+    CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double bn = n->bnorm;
+    double rel = bn > 0.0 ? std::sqrt(n->hsc->os.rr) / bn : 0.0;
+    int outer = 0;
+    long long inner_total = 0, launches = 0;
+    float inner_ms = 0.f;
+    int fallback = 0;
+    net_status status = NET_OK;
+    double rel_prev = rel;
+    while (true) {
+        if (rel <= o.tol_rel || bn == 0.0) break;
+        if (outer >= o.max_outer) { status = NET_ENOTCONVERGED; break; }
+        CK(cudaEventRecord(n->ev[1], st));
+        long long chunks = 0;
+        InnerScal *hs = &n->hsc->in[f32 ? 0 : 1];
+        InnerScal *ds = &n->dsc->in[f32 ? 0 : 1];
+        const int k = f32 ? 0 : 1;
+        // keep one chunk in flight ahead of the flag read
+        CK(cudaGraphLaunch(n->gexec[k], st));
+        chunks++;
+        while (true) {
+            CK(cudaMemcpyAsync(hs, ds, sizeof(InnerScal), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(n->ev[2], st));
+            CK(cudaGraphLaunch(n->gexec[k], st));
+            chunks++;
+            CK(cudaEventSynchronize(n->ev[2]));
+            if (hs->stop) break;
+            if ((chunks - 2) * (long long)n->gk[k] > o.max_inner) {
+                // the device cap should have stopped the loop by now
+                set_error("inner loop did not stop after %lld launches", chunks * (long long)n->gk[k]);
+                return r->status = NET_ETIMEOUT;
+            }
+        }
+        CK(cudaEventRecord(n->ev[2], st));
+        CK(cudaEventSynchronize(n->ev[2]));
+        CK(cudaMemcpyAsync(hs, ds, sizeof(InnerScal), cudaMemcpyDeviceToHost, st));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, n->ev[1], n->ev[2]));
+        CK(cudaStreamSynchronize(st));
+        inner_ms += ms;
+        launches += chunks * n->gk[k];
+        inner_total += hs->iter;
+        outer++;
+        // apply the correction, new residual; arm the same precision again
+        int next_f32 = f32;
+        oa = outer_args(n, next_f32, 1, f32, o);
+        CK(launch_outer(oa, st));
+        CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rel = std::sqrt(n->hsc->os.rr) / bn;
+        // a refinement step that gains less than 2x: continue in FP64
+        if (f32 && rel > o.tol_rel && rel > 0.5 * rel_prev) {
+            f32 = 0;
+            fallback = 1;
+            s = ensure_precision(n, 0);
+            if (s != NET_OK) return r->status = s;
+            s = ensure_graph(n, 0, K);
+            if (s != NET_OK) return r->status = s;
+            // re-arm the FP64 inner solve from the current x (no correction pending)
+            oa = outer_args(n, 0, 0, 0, o);
+            CK(launch_outer(oa, st));
+            CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            rel = std::sqrt(n->hsc->os.rr) / bn;
+        }
+        rel_prev = rel;
+    }
+    CK(cudaEventRecord(n->ev[2], st));
+    CK(cudaEventSynchronize(n->ev[2]));
+    float total_ms = 0.f;
+    CK(cudaEventElapsedTime(&total_ms, n->ev[0], n->ev[2]));
+    const OuterScal &os = n->hsc->os;
+    r->q_in = os.qin;
+    r->q_out = os.qout;
+    r->g_eff = os.qin / dP;
+    double S = 1.0;
+    const long long ext[3] = {G.nx, G.ny, G.nz};
+    for (int a = 0; a < G.ndim; a++)
+        if (a != G.f) S *= (double)ext[a];
+    r->k_eff = r->g_eff * (double)(G.nf - 1) / S;
+    r->rel_residual = rel;
+    r->max_imbalance = os.rmax;
+    r->energy_g = os.energy / (dP * dP);
+    r->n_active = n->n_active;
+    r->outer_iters = outer;
+    r->inner_iters = inner_total;
+    r->fp64_fallback = fallback;
+    r->ms = total_ms;
+    r->inner_ms = inner_ms;
+    r->inner_launches = launches;
+    r->status = status;
+    n->last = *r;
+    n->solved = true;
+    if (status != NET_OK) set_error("not converged: relative residual %.3e after %d refinement steps", rel, outer);
+    return status;
+}
+
+}  // namespace netsolve
+
+// ---------------------------------------------------------------------------
+// exported C ABI
+// ---------------------------------------------------------------------------
+#define NET_API extern "C" __attribute__((visibility("default")))
+
+NET_API void net_opts_default(net_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = NET_MIXED;
+    o->tol_rel = 1e-11;
+    o->tol_inner = 1e-4;
+    o->max_outer = 40;
+    o->max_inner = 200000;
+    o->check_every = 0;
+}
+
+NET_API net_status net_create(const net_desc *desc, const void *const g[3], net_t **out) {
+    return create_network(desc, g, out);
+}
+
+NET_API net_status net_solve(net_t *net, const net_opts *opts, net_result *out) {
+    if (!net || !out) { set_error("net_solve: NULL argument"); return NET_EINVAL; }
+    DevGuard dg(net->device);
+    return solve_impl(net, opts, out);
+}
+
+NET_API net_status net_flux(net_t *net, double *q_in, double *q_out, double *g_eff) {
+    if (!net) { set_error("net_flux: NULL handle"); return NET_EINVAL; }
+    if (!net->solved) { set_error("net_flux: no solve yet"); return NET_EINVAL; }
+    if (q_in) *q_in = net->last.q_in;
+    if (q_out) *q_out = net->last.q_out;
+    if (g_eff) *g_eff = net->last.g_eff;
+    return NET_OK;
+}
+
+NET_API net_status net_get_pressure(net_t *net, double *dst, int64_t n, int dst_on_device) {
+    if (!net || !dst) { set_error("net_get_pressure: NULL argument"); return NET_EINVAL; }
+    const Geom &G = net->g;
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    if (n < N) { set_error("net_get_pressure: buffer holds %lld < %lld", (long long)n, N); return NET_EINVAL; }
+    DevGuard dg(net->device);
+    cudaStream_t st = net->stream;
+    if (dst_on_device) {
+        CK(launch_unpack_x(G, net->x, dst, st));
+        CK(cudaStreamSynchronize(st));
+        return NET_OK;
+    }
+    double *tmp = nullptr;
+    CK(dalloc(&tmp, sizeof(double) * (size_t)N, st));
+    CK(launch_unpack_x(G, net->x, tmp, st));
+    CK(cudaMemcpyAsync(dst, tmp, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st));
+    dfree(tmp, st);
+    CK(cudaStreamSynchronize(st));
+    return NET_OK;
+}
+
+NET_API net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int64_t n) {
+    if (!net) { set_error("net_get_labels: NULL handle"); return NET_EINVAL; }
+    const Geom &G = net->g;
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    if (n < N) { set_error("net_get_labels: buffer holds %lld < %lld", (long long)n, N); return NET_EINVAL; }
+    DevGuard dg(net->device);
+    cudaStream_t st = net->stream;
+    int *dl = nullptr;
+    uint8_t *dc = nullptr;
+    CK(dalloc(&dl, sizeof(int) * (size_t)N, st));
+    CK(dalloc(&dc, (size_t)N, st));
+    CK(launch_unpack_labels(G, net->parent, net->cls, dl, dc, st));
+    if (label) CK(cudaMemcpyAsync(label, dl, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, st));
+    if (cls) CK(cudaMemcpyAsync(cls, dc, (size_t)N, cudaMemcpyDeviceToHost, st));
+    dfree(dl, st);
+    dfree(dc, st);
+    CK(cudaStreamSynchronize(st));
+    return NET_OK;
+}
+
+NET_API net_status net_destroy(net_t *net) {
+    if (!net) return NET_OK;
+    DevGuard dg(net->device);
+    release_network(net);
+    return NET_OK;
+}
+
+NET_API const char *net_last_error(void) { return last_error(); }

@@ -1,0 +1,57 @@
+// runtime_internal.h -- the network object behind net_t (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/netsolve.h"
+#include "kernels.h"
+
+namespace netsolve {
+
+// Device-resident scalars of one network (one allocation).
+struct DevScal {
+    InnerScal in[2];  // [0] FP32 inner solve, [1] FP64 inner solve
+    OuterScal os;
+    SetupScal ss;
+};
+
+}  // namespace netsolve
+
+struct net_s {
+    int device = 0;
+    netsolve::Geom g{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int raw_f32 = 0;
+    void *graw[3] = {nullptr, nullptr, nullptr};  // padded raw bonds
+    int *parent = nullptr;                         // union-find roots (padded index)
+    uint8_t *cls = nullptr;                        // cluster classes
+    double *dis = nullptr;                         // D^-1/2 on solved nodes, else 0
+    double *x = nullptr;                           // FP64 pressures
+    void *gs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // scaled bonds [f32, f64]
+    void *vec[2] = {nullptr, nullptr};            // y, r0, r1, p0, p1, q0, q1 per precision
+    double *partials = nullptr;
+    netsolve::DevScal *dsc = nullptr;              // device scalars
+    netsolve::DevScal *hsc = nullptr;              // pinned host mirror
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gk[2] = {0, 0};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    net_result last{};
+    bool solved = false;
+    double bnorm = 0.0;
+    long long n_active = 0;
+};
+
+namespace netsolve {
+void set_error(const char *fmt, ...);
+const char *last_error();
+net_status cuda_fail(cudaError_t e, const char *what);
+net_status make_geom(const net_desc *d, Geom *g);
+long long plane_elems(const Geom &g, int d);
+size_t net_footprint_bytes(const Geom &g, int raw_f32);
+InnerArgs inner_args(net_t *n, int f32);
+OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op);
+net_status setup_network(net_t *n, const void *const g[3], int on_device);
+void release_network(net_t *n);
+net_status create_network(const net_desc *desc, const void *const g[3], net_t **out);
+net_status solve_impl(net_t *n, const net_opts *o, net_result *r);
+}  // namespace netsolve

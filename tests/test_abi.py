@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares (no GPU needed: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "netsolve.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(net[q]?_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_1908_03301_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ["net_create", "net_solve", "net_flux", "net_get_pressure", "net_get_labels",
+              "net_destroy", "net_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(so):
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_match_header():
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    assert sorted(ns.EXPORTS) == declared_functions()
+
+
+def test_host_side_validation_without_gpu(so):
+    """Descriptor checks happen on the host before any device work."""
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns._lib = None
+    L = ns.lib()
+    h = ctypes.c_void_p()
+    ptrs = (ctypes.c_void_p * 3)()
+    for dims, fa in [((2, 8), 0), ((8, 8), 2), ((0, 8), 0)]:
+        d = ns.make_desc(dims, flow_axis=fa)
+        assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
+        assert L.net_last_error()
+    d = ns.make_desc((8, 8))
+    d.periodic_mask = 1
+    assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
+    d = ns.make_desc((8, 8), p_in=1.0, p_out=1.0)
+    assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
+    assert L.net_solve(None, None, None) == ns.NET_EINVAL
+    assert L.net_destroy(None) == ns.NET_OK
