@@ -185,6 +185,33 @@ net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int64_t n);
 /* Release the network's device state.  NULL is accepted. */
 net_status net_destroy(net_t *net);
 
+/*
+ * Cluster labels without any memory allocation.  (The paper has no
+ * counterpart; this serves callers that cannot allocate device memory when
+ * they need labels: code inside a framework whose pool owns all device memory,
+ * or a latency-critical loop where cudaMalloc / cudaFree, which may block the
+ * host and synchronise the device, are not acceptable.)
+ *
+ * Computes the same labels and classes as net_create + net_get_labels.
+ *   desc    as for net_create; desc->on_device must be 1; desc->stream is
+ *           the stream the work runs on (NULL = the default stream).
+ *   g[d]    device bond planes (compact layout, desc->bond_dtype).
+ *   label   device output, N int32 (may be NULL); cls: device output, N uint8
+ *           (may be NULL).  N = nx*ny*nz.
+ * The union-find scratch is a fixed array inside the library's device image,
+ * sized for NET_NOALLOC_MAX_NODES nodes (8 MiB); every GPU that loads the
+ * library holds it until the process exits.  N above that limit returns
+ * NET_EINVAL.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array, so
+ * calls that overlap on the GPU (other streams or threads) race: keep them
+ * ordered.  The call returns after the work on desc->stream has finished;
+ * NET_EINVAL also for a negative, NaN or infinite conductance.
+ */
+#define NET_NOALLOC_MAX_NODES (1LL << 20)
+net_status net_labels_noalloc(const net_desc *desc, const void *const g[3], int32_t *label,
+                              uint8_t *cls);
+
 /* Thread-local message describing the last failing call on this thread. */
 const char *net_last_error(void);
 

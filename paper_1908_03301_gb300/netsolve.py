@@ -48,7 +48,7 @@ class net_result(C.Structure):
 
 
 EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_pressure",
-           "net_get_labels", "net_destroy", "net_last_error"]
+           "net_get_labels", "net_destroy", "net_last_error", "net_labels_noalloc"]
 
 _lib = None
 
@@ -82,6 +82,8 @@ def lib(build_if_missing: bool = False):
     L.net_destroy.restype = C.c_int
     L.net_last_error.argtypes = []
     L.net_last_error.restype = C.c_char_p
+    L.net_labels_noalloc.argtypes = [P(net_desc), P(vp), vp, vp]
+    L.net_labels_noalloc.restype = C.c_int
     if hasattr(L, "net_solve_batch"):
         L.net_solve_batch.argtypes = [P(vp), C.c_int, P(net_opts), P(net_result)]
         L.net_solve_batch.restype = C.c_int
