@@ -58,7 +58,9 @@ struct InnerScal {
     long long iter;       // iteration kernels that did work in this solve
     long long max_iter;
     long long stag_window;
-    int stop;             // 0 run, 1 converged, 2 cap, 3 stagnated, 4 breakdown
+    int stop;             // 0 run, 1 converged, 2 cap, 3 stagnated, 4 breakdown,
+                          // 5 device wait timed out
+    int err;              // set by a CTA whose bounded wait gave up
     unsigned int counter; // CTA arrival counter of the running launch
 };
 
@@ -150,6 +152,39 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], const int (&ops)[NV
     block_reduce<NV, NT>(v, ops);
     if (threadIdx.x == 0) *counter = 0u;
     return true;
+}
+
+// End of one fused CG iteration, run by one thread of the last CTA with the
+// four reduced sums v = {<p,q>, <r,q>, <q,q>, <r,r>} of iteration k:
+// alpha_k = <r,r>/<p,q>, beta_k = ||r - alpha q||^2 / <r,r> with the square
+// expanded; convergence, cap, stagnation and breakdown tests.
+__device__ __forceinline__ void finish_iteration(InnerScal *s, long long k, const double (&v)[4]) {
+    const double pq = v[0], rq = v[1], qq = v[2], rr = v[3];
+    s->rho = rr;
+    s->iter = k + 1;
+    if (s->err) {
+        s->stop = 5;
+        return;
+    }
+    if (rr <= s->tol2 * s->rho0 || rr == 0.0) {
+        s->stop = 1;
+        return;
+    }
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rr)) {
+        s->stop = 4;
+        return;
+    }
+    const double a = rr / pq;
+    double rn1 = rr - 2.0 * a * rq + a * a * qq;
+    if (!(rn1 > 0.0)) rn1 = 0.0;  // cancellation: restart along the residual
+    s->alpha = a;
+    s->beta = rn1 / rr;
+    if (rr < 0.25 * s->best) {
+        s->best = rr;
+        s->best_iter = k;
+    }
+    if (k + 1 >= s->max_iter) s->stop = 2;
+    else if (k - s->best_iter > s->stag_window) s->stop = 3;
 }
 
 // 16-byte vector of T (float4 / double2) with element access.

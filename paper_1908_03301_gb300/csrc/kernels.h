@@ -43,6 +43,15 @@ struct InnerArgs {
 // Number of CTAs the inner iteration kernel uses for this geometry.
 int inner_grid_blocks(const Geom &g, int f32);
 cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st);
+// Kernel attributes the inner kernel needs; call before launching or
+// capturing it.
+cudaError_t prepare_inner(const Geom &g, int f32);
+
+// ---- persistent 2D row march (kernels_march.cu) ----------------------------
+bool march_applies(const Geom &g);
+int march_blocks(const Geom &g, int f32);
+cudaError_t march_prepare(int f32);
+cudaError_t launch_march(const InnerArgs &a, int f32, cudaStream_t st);
 
 struct OuterArgs {
     Geom g;

@@ -230,30 +230,7 @@ inner_iter_kernel(Geom g, const T *__restrict__ g0, const T *__restrict__ g1,
     double v[4] = {(double)a_pq, (double)a_rq, (double)a_qq, (double)a_rr};
     const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM};
     if (!grid_reduce<4, NT>(v, ops, partials, &s->counter)) return;
-    if (threadIdx.x != 0) return;
-    const double pq = v[0], rq = v[1], qq = v[2], rr = v[3];
-    const long long k = iter;
-    s->rho = rr;
-    s->iter = k + 1;
-    if (rr <= s->tol2 * s->rho0 || rr == 0.0) {
-        s->stop = 1;
-        return;
-    }
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rr)) {
-        s->stop = 4;
-        return;
-    }
-    const double a = rr / pq;
-    double rn1 = rr - 2.0 * a * rq + a * a * qq;
-    if (!(rn1 > 0.0)) rn1 = 0.0;  // cancellation: restart along the residual
-    s->alpha = a;
-    s->beta = rn1 / rr;
-    if (rr < 0.25 * s->best) {
-        s->best = rr;
-        s->best_iter = k;
-    }
-    if (k + 1 >= s->max_iter) s->stop = 2;
-    else if (k - s->best_iter > s->stag_window) s->stop = 3;
+    if (threadIdx.x == 0) finish_iteration(s, iter, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,6 +340,8 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     is->iter = 0;
     is->max_iter = max_inner;
     is->stag_window = stag_window;
+    is->err = 0;
+    is->counter = 0u;
     is->stop = v[2] > 0.0 ? 0 : 1;
 }
 
@@ -413,11 +392,17 @@ inline long long nblocks(dim3 d) { return (long long)d.x * d.y * d.z; }
 }  // namespace
 
 int inner_grid_blocks(const Geom &g, int f32) {
+    if (march_applies(g)) return march_blocks(g, f32);
     if (g.ndim == 2) return (int)nblocks(f32 ? inner_grid<float, 2>(g) : inner_grid<double, 2>(g));
     return (int)nblocks(f32 ? inner_grid<float, 3>(g) : inner_grid<double, 3>(g));
 }
 
+cudaError_t prepare_inner(const Geom &g, int f32) {
+    return march_applies(g) ? march_prepare(f32) : cudaSuccess;
+}
+
 cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st) {
+    if (march_applies(a.g)) return launch_march(a, f32, st);
     if (a.g.ndim == 2) return f32 ? launch_inner_t<float, 2>(a, st) : launch_inner_t<double, 2>(a, st);
     return f32 ? launch_inner_t<float, 3>(a, st) : launch_inner_t<double, 3>(a, st);
 }

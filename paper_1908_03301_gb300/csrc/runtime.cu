@@ -153,6 +153,7 @@ net_status ensure_graph(net_t *n, int f32, int K) {
         n->gexec[k] = nullptr;
     }
     InnerArgs a = inner_args(n, f32);
+    CK(prepare_inner(n->g, f32));
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -414,6 +415,10 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         inner_ms += ms;
         launches += chunks * n->gk[k];
         inner_total += hs->iter;
+        if (hs->stop == 5) {
+            set_error("a bounded device wait in the CG kernel gave up");
+            return r->status = NET_ETIMEOUT;
+        }
         outer++;
         // apply the correction, new residual; arm the same precision again
         int next_f32 = f32;
