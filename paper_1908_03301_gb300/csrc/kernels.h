@@ -43,15 +43,35 @@ struct InnerArgs {
 // Number of CTAs the inner iteration kernel uses for this geometry.
 int inner_grid_blocks(const Geom &g, int f32);
 cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st);
-// Kernel attributes the inner kernel needs; call before launching or
-// capturing it.
-cudaError_t prepare_inner(const Geom &g, int f32);
 
-// ---- persistent 2D row march (kernels_march.cu) ----------------------------
-bool march_applies(const Geom &g);
-int march_blocks(const Geom &g, int f32);
-cudaError_t march_prepare(int f32);
-cudaError_t launch_march(const InnerArgs &a, int f32, cudaStream_t st);
+// ---- whole inner solve of a 2D network in one launch (cg_persist.cu) ------
+struct PersistArgs {
+    Geom g;
+    const float *gx, *gy;      // scaled bonds
+    float *y, *r, *p, *q;      // inner vectors, updated in place
+    InnerScal *s;              // armed state in, final state out
+    float *hb;                 // halo copies [2][grid][2][3][px]
+    float *pb;                 // per-CTA sums [2][grid][4]
+    InnerScal *bc;             // state published by the barrier [2]
+    unsigned *bar_count;       // grid barrier: arrivals (bar_count[0]) and
+    unsigned *bar_gen;         //   generation (bar_gen == bar_count + 1)
+    int *err;
+};
+bool persist_applies(const Geom &g, int f32);
+int persist_grid(const Geom &g);
+cudaError_t persist_prepare();
+cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st);
+
+// ---- persistent sweep over segmented networks (sweep.cu) -------------------
+struct SweepInst;
+struct SweepSeg;
+int sweep_max_width(int ndim, int f32);
+int sweep_vt(int f32);
+int sweep_consumers();
+cudaError_t sweep_prepare(int ndim, int f32);
+cudaError_t launch_sweep(int ndim, int f32, int grid, const SweepInst *insts, const SweepSeg *segs,
+                         const int *cta_begin, cudaStream_t st);
+
 
 struct OuterArgs {
     Geom g;

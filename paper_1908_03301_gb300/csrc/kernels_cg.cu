@@ -392,17 +392,11 @@ inline long long nblocks(dim3 d) { return (long long)d.x * d.y * d.z; }
 }  // namespace
 
 int inner_grid_blocks(const Geom &g, int f32) {
-    if (march_applies(g)) return march_blocks(g, f32);
     if (g.ndim == 2) return (int)nblocks(f32 ? inner_grid<float, 2>(g) : inner_grid<double, 2>(g));
     return (int)nblocks(f32 ? inner_grid<float, 3>(g) : inner_grid<double, 3>(g));
 }
 
-cudaError_t prepare_inner(const Geom &g, int f32) {
-    return march_applies(g) ? march_prepare(f32) : cudaSuccess;
-}
-
 cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st) {
-    if (march_applies(a.g)) return launch_march(a, f32, st);
     if (a.g.ndim == 2) return f32 ? launch_inner_t<float, 2>(a, st) : launch_inner_t<double, 2>(a, st);
     return f32 ? launch_inner_t<float, 3>(a, st) : launch_inner_t<double, 3>(a, st);
 }

@@ -13,11 +13,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/netsolve.h"
 #include "kernels.h"
+#include "plan.h"
 #include "runtime_internal.h"
 
 using namespace netsolve;
@@ -69,7 +72,9 @@ net_status make_geom(const net_desc *d, Geom *g) {
     G.px = (int)round_up(G.nx, 4);
     G.nf = (int)d->n[d->flow_axis];
     G.plane = (long long)G.px * G.ny;
-    G.pad = round_up(d->ndim == 3 ? G.plane : (long long)G.px, 64);
+    // zeros before and after the grid: one plane (3D) or row (2D) for the
+    // stencil, plus a row and 16 bytes for the halo rows the sweep copies
+    G.pad = round_up((d->ndim == 3 ? G.plane : (long long)G.px) + G.px + 64, 64);
     G.len = G.pad + G.plane * G.nz + G.pad;
     G.p_in = d->p_in;
     G.p_out = d->p_out;
@@ -145,6 +150,75 @@ net_status ensure_precision(net_t *n, int f32) {
     return NET_OK;
 }
 
+// NETSOLVE_KERNEL selects the inner-loop kernel for comparisons:
+// "persist" (default where it applies), "sweep" or "tiled".
+bool use_sweep_kernel() {
+    const char *e = getenv("NETSOLVE_KERNEL");
+    return !(e && strcmp(e, "tiled") == 0);
+}
+
+bool use_persist_kernel(const net_t *n, int f32) {
+    const char *e = getenv("NETSOLVE_KERNEL");
+    if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0)) return false;
+    return persist_applies(n->g, f32);
+}
+
+net_status ensure_persist(net_t *n) {
+    if (n->ps_hb) return NET_OK;
+    cudaStream_t st = n->stream;
+    const int grid = persist_grid(n->g);
+    // halo copies: [sweep parity][CTA][first/last row][r, q, p][px]
+    CK(dalloc(&n->ps_hb, sizeof(float) * 2 * 2 * 3 * (size_t)grid * n->g.px, st));
+    CK(dalloc(&n->ps_pb, sizeof(float) * 2 * 4 * (size_t)grid, st));
+    CK(dalloc(&n->ps_bc, sizeof(InnerScal) * 2, st));
+    CK(dalloc(&n->ps_bar, sizeof(unsigned) * 2, st));
+    CK(dalloc(&n->ps_err, sizeof(int), st));
+    CK(persist_prepare());
+    n->ps_grid = grid;
+    return NET_OK;
+}
+
+int device_sm_count(int dev) {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        nsm = 152;
+    return nsm;
+}
+
+// Plan the sweep for this one network and upload it (per precision).
+net_status ensure_sweep_plan(net_t *n, int f32) {
+    const int k = f32 ? 0 : 1;
+    if (n->sw[k].segs) return NET_OK;
+    cudaStream_t st = n->stream;
+    HostPlan hp;
+    std::vector<PlanNet> nets{PlanNet{n->g, true}};
+    build_plan(nets, n->g.ndim, f32, device_sm_count(n->device), 1, hp);
+    SweepDev &sd = n->sw[k];
+    sd.grid = hp.grid;
+    CK(dalloc(&sd.segs, sizeof(SweepSeg) * hp.segs.size(), st));
+    CK(dalloc(&sd.cta, sizeof(int) * hp.cta_begin.size(), st));
+    CK(dalloc(&sd.part, sizeof(double) * 4 * (size_t)std::max(1, hp.nseg[0]), st));
+    CK(dalloc(&sd.inst, sizeof(SweepInst), st));
+    InnerArgs a = inner_args(n, f32);
+    SweepInst si{};
+    si.g = n->g;
+    for (int d = 0; d < 3; d++) si.gs[d] = a.gs[d];
+    si.y = a.y;
+    for (int j = 0; j < 2; j++) {
+        si.r[j] = a.r[j];
+        si.p[j] = a.p[j];
+        si.q[j] = a.q[j];
+    }
+    si.s = a.s;
+    si.part = sd.part;
+    si.nseg = hp.nseg[0];
+    CK(cudaMemcpyAsync(sd.segs, hp.segs.data(), sizeof(SweepSeg) * hp.segs.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sd.cta, hp.cta_begin.data(), sizeof(int) * hp.cta_begin.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sd.inst, &si, sizeof(SweepInst), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return NET_OK;
+}
+
 net_status ensure_graph(net_t *n, int f32, int K) {
     const int k = f32 ? 0 : 1;
     if (n->gexec[k] && n->gk[k] == K) return NET_OK;
@@ -153,12 +227,20 @@ net_status ensure_graph(net_t *n, int f32, int K) {
         n->gexec[k] = nullptr;
     }
     InnerArgs a = inner_args(n, f32);
-    CK(prepare_inner(n->g, f32));
+    const bool sweep = use_sweep_kernel();
+    if (sweep) {
+        net_status s = ensure_sweep_plan(n, f32);
+        if (s != NET_OK) return s;
+        CK(sweep_prepare(n->g.ndim, f32));
+    }
+    const SweepDev &sd = n->sw[k];
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    for (int i = 0; e == cudaSuccess && i < K; i++) e = launch_inner_iter(a, f32, cs);
+    for (int i = 0; e == cudaSuccess && i < K; i++)
+        e = sweep ? launch_sweep(n->g.ndim, f32, sd.grid, sd.inst, sd.segs, sd.cta, cs)
+                  : launch_inner_iter(a, f32, cs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&n->gexec[k], graph, 0);
@@ -274,10 +356,19 @@ void release_network(net_t *n) {
     cudaStream_t st = n->stream;
     for (int k = 0; k < 2; k++) {
         if (n->gexec[k]) cudaGraphExecDestroy(n->gexec[k]);
+        dfree(n->sw[k].segs, st);
+        dfree(n->sw[k].cta, st);
+        dfree(n->sw[k].part, st);
+        dfree(n->sw[k].inst, st);
         for (int d = 0; d < 3; d++) dfree(n->gs[k][d], st);
         dfree(n->vec[k], st);
     }
     for (int d = 0; d < 3; d++) dfree(n->graw[d], st);
+    dfree(n->ps_hb, st);
+    dfree(n->ps_pb, st);
+    dfree(n->ps_bc, st);
+    dfree(n->ps_bar, st);
+    dfree(n->ps_err, st);
     dfree(n->parent, st);
     dfree(n->cls, st);
     dfree(n->dis, st);
@@ -348,8 +439,10 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     }
     net_status s = ensure_precision(n, f32);
     if (s != NET_OK) return r->status = s;
-    s = ensure_graph(n, f32, K);
-    if (s != NET_OK) return r->status = s;
+    if (!use_persist_kernel(n, f32)) {
+        s = ensure_graph(n, f32, K);
+        if (s != NET_OK) return r->status = s;
+    }
 
     CK(cudaEventRecord(n->ev[0], st));
     // fresh start: initial pressures, then the caller's guess
@@ -390,6 +483,38 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         InnerScal *hs = &n->hsc->in[f32 ? 0 : 1];
         InnerScal *ds = &n->dsc->in[f32 ? 0 : 1];
         const int k = f32 ? 0 : 1;
+        if (use_persist_kernel(n, f32)) {
+            // the whole inner solve in one cooperative launch
+            s = ensure_persist(n);
+            if (s != NET_OK) return r->status = s;
+            InnerArgs ia = inner_args(n, 1);
+            PersistArgs pa{};
+            pa.g = G;
+            pa.gx = (const float *)ia.gs[0];
+            pa.gy = (const float *)ia.gs[1];
+            pa.y = (float *)ia.y;
+            pa.r = (float *)ia.r[0];
+            pa.p = (float *)ia.p[0];
+            pa.q = (float *)ia.q[0];
+            pa.s = ds;
+            pa.hb = n->ps_hb;
+            pa.pb = n->ps_pb;
+            pa.bc = n->ps_bc;
+            pa.bar_count = n->ps_bar;
+            pa.bar_gen = n->ps_bar + 1;
+            pa.err = n->ps_err;
+            CK(launch_persist(pa, n->ps_grid, st));
+            chunks = 0;
+            launches += 1;
+            CK(cudaMemcpyAsync(&n->hsc->perr, n->ps_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hs, ds, sizeof(InnerScal), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(n->ev[2], st));
+            CK(cudaEventSynchronize(n->ev[2]));
+            if (n->hsc->perr) {
+                set_error("a bounded device wait in the persistent CG kernel gave up");
+                return r->status = NET_ETIMEOUT;
+            }
+        } else {
         // keep one chunk in flight ahead of the flag read
         CK(cudaGraphLaunch(n->gexec[k], st));
         chunks++;
@@ -409,6 +534,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         CK(cudaEventRecord(n->ev[2], st));
         CK(cudaEventSynchronize(n->ev[2]));
         CK(cudaMemcpyAsync(hs, ds, sizeof(InnerScal), cudaMemcpyDeviceToHost, st));
+        }
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, n->ev[1], n->ev[2]));
         CK(cudaStreamSynchronize(st));
@@ -433,8 +559,10 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             fallback = 1;
             s = ensure_precision(n, 0);
             if (s != NET_OK) return r->status = s;
-            s = ensure_graph(n, 0, K);
-            if (s != NET_OK) return r->status = s;
+            if (!use_persist_kernel(n, 0)) {
+                s = ensure_graph(n, 0, K);
+                if (s != NET_OK) return r->status = s;
+            }
             // re-arm the FP64 inner solve from the current x (no correction pending)
             oa = outer_args(n, 0, 0, 0, o);
             CK(launch_outer(oa, st));

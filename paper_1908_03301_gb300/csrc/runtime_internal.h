@@ -4,14 +4,25 @@
 
 #include "../../include/netsolve.h"
 #include "kernels.h"
+#include "sweep.cuh"
 
 namespace netsolve {
+
+// Device copy of a sweep plan (segments, per-CTA offsets, network record).
+struct SweepDev {
+    SweepSeg *segs = nullptr;
+    int *cta = nullptr;
+    double *part = nullptr;
+    SweepInst *inst = nullptr;
+    int grid = 0;
+};
 
 // Device-resident scalars of one network (one allocation).
 struct DevScal {
     InnerScal in[2];  // [0] FP32 inner solve, [1] FP64 inner solve
     OuterScal os;
     SetupScal ss;
+    int perr;  // host mirror of the persistent kernel's error word
 };
 
 }  // namespace netsolve
@@ -33,6 +44,15 @@ struct net_s {
     netsolve::DevScal *dsc = nullptr;              // device scalars
     netsolve::DevScal *hsc = nullptr;              // pinned host mirror
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    netsolve::SweepDev sw[2];                      // sweep plan per precision
+    // whole-solve persistent kernel (2D, FP32): halo rows, partials, grid
+    // barrier words, error word
+    float *ps_hb = nullptr;
+    float *ps_pb = nullptr;
+    netsolve::InnerScal *ps_bc = nullptr;
+    unsigned *ps_bar = nullptr;
+    int *ps_err = nullptr;
+    int ps_grid = 0;
     int gk[2] = {0, 0};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     net_result last{};
