@@ -212,6 +212,60 @@ net_status net_destroy(net_t *net);
 net_status net_labels_noalloc(const net_desc *desc, const void *const g[3], int32_t *label,
                               uint8_t *cls);
 
+/*
+ * Solve `count` independent networks together.  Every sweep of the CG loop
+ * (Sec. IV) is one launch of a kernel with one CTA per SM that walks all
+ * running networks' segments; each network keeps its own CG scalars and its
+ * own convergence mask, and networks drop out as they converge while the
+ * rest continue.  The sweeps run as CUDA-graph chunks of opts->check_every
+ * launches (0 = 16).  res[i] receives network i's result; each result
+ * matches the network's stand-alone net_solve within the solver tolerance.
+ * All networks must live on the current device.  opts NULL = defaults (one
+ * opts for all; x0 is ignored).  Returns NET_OK if every network converged,
+ * else the first non-OK status (each res[i].status says which).
+ */
+net_status net_solve_batch(net_t *const *nets, int count, const net_opts *opts,
+                           net_result *res);
+
+/*
+ * Continuous-batching queue.  Requests are admitted while their device
+ * footprint fits in mem_budget_bytes and a slot among max_slots is free;
+ * admitted requests are solved together with those already running, and
+ * finished ones leave at once, freeing memory and a slot for the next.
+ * A background host thread drives the device.  opts applies to every request
+ * (NULL = defaults).
+ */
+net_status netq_create(size_t mem_budget_bytes, int max_slots, const net_opts *opts,
+                       netq_t **out);
+
+/*
+ * Submit a network (arguments as for net_create; host bond pointers only,
+ * copied before the call returns).  *ticket identifies the request.
+ * NET_EBUDGET if the request's estimated device footprint alone exceeds the
+ * memory budget; NET_EINVAL for a bad descriptor.  Conductance errors found
+ * on the device are reported through the request's result status.
+ */
+net_status netq_submit(netq_t *q, const net_desc *desc, const void *const g[3],
+                       uint64_t *ticket);
+
+/* Non-blocking: NET_EBUSY while the request is queued or running, else its
+ * final status with *out filled; a finished ticket can be read once. */
+net_status netq_poll(netq_t *q, uint64_t ticket, net_result *out);
+
+/* Block up to timeout_ms (< 0: no limit) for the request; NET_ETIMEOUT if it
+ * is still pending. */
+net_status netq_wait(netq_t *q, uint64_t ticket, int timeout_ms, net_result *out);
+
+/* Cancel a queued (not yet admitted) request: its status becomes
+ * NET_ECANCELLED.  NET_EBUSY if it is already running. */
+net_status netq_cancel(netq_t *q, uint64_t ticket);
+
+/* Latency statistics over finished requests (arrival to result, ms). */
+net_status netq_stats(netq_t *q, double *p50_ms, double *p99_ms, uint64_t *completed);
+
+/* Stop the worker (pending requests finish as NET_ECANCELLED) and free. */
+net_status netq_destroy(netq_t *q);
+
 /* Thread-local message describing the last failing call on this thread. */
 const char *net_last_error(void);
 

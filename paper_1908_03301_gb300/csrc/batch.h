@@ -1,0 +1,79 @@
+// batch.h -- many networks solved together (internal).
+//
+// The engine keeps a set of networks whose refinement loops are in flight.
+// Networks are grouped by (dimension, inner precision); each group has one
+// sweep plan (all its running networks' segments dealt over the SMs) and a
+// CUDA graph of K sweep launches.  step() replays every group's graph once,
+// gathers all stop flags with one small kernel and one read, and runs the
+// FP64 outer pass of every network whose inner solve stopped; those
+// networks then continue, switch to FP64, or finish.  Finished networks
+// leave at once, so the others' sweeps get cheaper.
+#pragma once
+#include <chrono>
+#include <cstdint>
+#include <vector>
+
+#include "runtime_internal.h"
+
+namespace netsolve {
+
+struct BatchItem {
+    net_t *net = nullptr;
+    net_opts opts{};
+    int f32 = 1;             // inner precision in use
+    int outer = 0;
+    long long inner_total = 0;
+    double rel = 0.0, rel_prev = 0.0;
+    int fallback = 0;
+    bool done = false;
+    net_result res{};
+    uint64_t user = 0;       // caller's tag (queue ticket)
+    std::chrono::steady_clock::time_point t_start;
+};
+
+class BatchEngine {
+public:
+    BatchEngine(int device, cudaStream_t stream);
+    ~BatchEngine();
+    // Start the refinement loops of these networks (set-up launches for all,
+    // one synchronisation).  Items that need no iteration finish here.
+    net_status add(const std::vector<BatchItem *> &items);
+    // K sweeps for every running network, then the outer passes of those
+    // whose inner solve stopped.
+    net_status step(int K);
+    // Finished items since the last call.
+    std::vector<BatchItem *> take_done();
+    size_t running() const { return nrun_; }
+
+private:
+    struct Group {
+        int ndim = 2, f32 = 1;
+        std::vector<BatchItem *> items;
+        bool dirty = true;
+        SweepInst *d_inst = nullptr;
+        SweepSeg *d_segs = nullptr;
+        int *d_cta = nullptr;
+        double *d_part = nullptr;
+        size_t cap_inst = 0, cap_segs = 0, cap_part = 0;
+        int grid = 0, K = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    net_status rebuild(Group &g, int K);
+    net_status outer_pass(BatchItem *it, int apply_corr, int corr_f32);
+    void finish(BatchItem *it, net_status st);
+    Group &group_of(int ndim, int f32) { return groups_[ndim - 2][f32 ? 1 : 0]; }
+
+    int device_;
+    int nsm_;
+    cudaStream_t st_;
+    Group groups_[2][2];
+    size_t nrun_ = 0;
+    std::vector<BatchItem *> done_;
+    // stop-flag gather
+    const InnerScal **d_sptr_ = nullptr;
+    int *d_stop_ = nullptr;
+    long long *d_iter_ = nullptr;
+    size_t cap_g_ = 0;
+};
+
+}  // namespace netsolve

@@ -342,7 +342,8 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     is->stag_window = stag_window;
     is->err = 0;
     is->counter = 0u;
-    is->stop = v[2] > 0.0 ? 0 : 1;
+    // no inner solve when the outer tolerance is met (or nothing to solve)
+    is->stop = (v[2] > 0.0 && !(rel <= tol_rel)) ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------

@@ -110,19 +110,6 @@ namespace {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
     } while (0)
 
-template <typename T>
-cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
-    void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes ? bytes : 16, st);
-    if (e != cudaSuccess) return e;
-    *p = (T *)q;
-    return cudaMemsetAsync(q, 0, bytes ? bytes : 16, st);
-}
-
-void dfree(void *p, cudaStream_t st) {
-    if (p) cudaFreeAsync(p, st);
-}
-
 struct DevGuard {
     int prev = -1;
     explicit DevGuard(int dev) {
@@ -135,9 +122,10 @@ struct DevGuard {
     }
 };
 
-net_status ensure_precision(net_t *n, int f32) {
+}  // namespace
+
+net_status netsolve::ensure_precision(net_t *n, int f32, cudaStream_t st) {
     const int k = f32 ? 0 : 1;
-    cudaStream_t st = n->stream;
     const size_t L = (size_t)n->g.len;
     const size_t es = f32 ? 4 : 8;
     if (!n->gs[k][0]) {
@@ -149,6 +137,8 @@ net_status ensure_precision(net_t *n, int f32) {
     if (!n->vec[k]) CK(dalloc(&n->vec[k], 7 * L * es, st));
     return NET_OK;
 }
+
+namespace {
 
 // NETSOLVE_KERNEL selects the inner-loop kernel for comparisons:
 // "persist" (default where it applies), "sweep" or "tiled".
@@ -437,7 +427,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         CK(cudaEventRecord(n->ev[3], n->stream));
         CK(cudaStreamWaitEvent(st, n->ev[3], 0));
     }
-    net_status s = ensure_precision(n, f32);
+    net_status s = ensure_precision(n, f32, st);
     if (s != NET_OK) return r->status = s;
     if (!use_persist_kernel(n, f32)) {
         s = ensure_graph(n, f32, K);
@@ -557,7 +547,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         if (f32 && rel > o.tol_rel && rel > 0.5 * rel_prev) {
             f32 = 0;
             fallback = 1;
-            s = ensure_precision(n, 0);
+            s = ensure_precision(n, 0, st);
             if (s != NET_OK) return r->status = s;
             if (!use_persist_kernel(n, 0)) {
                 s = ensure_graph(n, 0, K);

@@ -62,6 +62,19 @@ struct net_s {
 };
 
 namespace netsolve {
+template <typename T>
+inline cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) return e;
+    *p = (T *)q;
+    return cudaMemsetAsync(q, 0, bytes ? bytes : 16, st);
+}
+inline void dfree(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+// Scaled bonds and inner vectors of one precision (allocated on first use).
+net_status ensure_precision(net_t *n, int f32, cudaStream_t st);
 void set_error(const char *fmt, ...);
 const char *last_error();
 net_status cuda_fail(cudaError_t e, const char *what);

@@ -615,51 +615,47 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
         v4[3] = (double)a_rr;
         }
         // ---- segment sums -> the network's slot; last arrival finishes ----
+        // CTA-level sums in T (FP32 for the mixed path: GB300's FP64 rate
+        // makes a 16-warp FP64 reduction cost microseconds); the final sum
+        // over the network's segments is FP64, in one warp.
+        T t4[4] = {(T)v4[0], (T)v4[1], (T)v4[2], (T)v4[3]};
 #pragma unroll
         for (int k = 0; k < 4; k++)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v4[k] += __shfl_xor_sync(0xffffffffu, v4[k], off);
+            for (int off = 16; off > 0; off >>= 1) t4[k] += __shfl_xor_sync(0xffffffffu, t4[k], off);
         if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < 4; k++) s_red[warp][k] = v4[k];
+            for (int k = 0; k < 4; k++) s_red[warp][k] = (double)t4[k];
         cons_sync();
         if (c == 0) {
-            double tot[4] = {0, 0, 0, 0};
+            T tot[4] = {T(0), T(0), T(0), T(0)};
             for (int wi = 0; wi < NCW; wi++)
 #pragma unroll
-                for (int k = 0; k < 4; k++) tot[k] += s_red[wi][k];
+                for (int k = 0; k < 4; k++) tot[k] += (T)s_red[wi][k];
             if (s_err) {
                 atomicExch(&I.s->err, 1);
-                tot[0] = tot[1] = tot[2] = tot[3] = 0.0;
+                tot[0] = tot[1] = tot[2] = tot[3] = T(0);
             }
 #pragma unroll
-            for (int k = 0; k < 4; k++) I.part[sg.slot * 4 + k] = tot[k];
+            for (int k = 0; k < 4; k++) I.part[sg.slot * 4 + k] = (double)tot[k];
             __threadfence();
             const unsigned int n = atomicAdd(&I.s->counter, 1u);
             s_last = (n == (unsigned)I.nseg - 1);
         }
         cons_sync();
-        if (s_last) {
+        if (s_last && warp == 0) {
             __threadfence();
             double tot[4] = {0, 0, 0, 0};
-            for (int i = c; i < I.nseg; i += NC)
+            for (int i = lane; i < I.nseg; i += 32)
 #pragma unroll
                 for (int k = 0; k < 4; k++) tot[k] += __ldcg(&I.part[i * 4 + k]);
 #pragma unroll
             for (int k = 0; k < 4; k++)
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], off);
-            if (lane == 0)
-#pragma unroll
-                for (int k = 0; k < 4; k++) s_red[warp][k] = tot[k];
-            cons_sync();
-            if (c == 0) {
-                double fin[4] = {0, 0, 0, 0};
-                for (int wi = 0; wi < NCW; wi++)
-#pragma unroll
-                    for (int k = 0; k < 4; k++) fin[k] += s_red[wi][k];
+            if (lane == 0) {
                 I.s->counter = 0u;
-                finish_iteration(I.s, I.s->iter, fin);
+                finish_iteration(I.s, I.s->iter, tot);
             }
         }
         cons_sync();  // s_red / s_last reused by the next segment

@@ -48,7 +48,9 @@ class net_result(C.Structure):
 
 
 EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_pressure",
-           "net_get_labels", "net_destroy", "net_last_error", "net_labels_noalloc"]
+           "net_get_labels", "net_destroy", "net_solve_batch", "netq_create", "netq_submit",
+           "netq_poll", "netq_wait", "netq_cancel", "netq_stats", "netq_destroy",
+           "net_last_error", "net_labels_noalloc"]
 
 _lib = None
 
@@ -84,10 +86,9 @@ def lib(build_if_missing: bool = False):
     L.net_last_error.restype = C.c_char_p
     L.net_labels_noalloc.argtypes = [P(net_desc), P(vp), vp, vp]
     L.net_labels_noalloc.restype = C.c_int
-    if hasattr(L, "net_solve_batch"):
+    if True:
         L.net_solve_batch.argtypes = [P(vp), C.c_int, P(net_opts), P(net_result)]
         L.net_solve_batch.restype = C.c_int
-    if hasattr(L, "netq_create"):
         L.netq_create.argtypes = [C.c_size_t, C.c_int, P(net_opts), P(vp)]
         L.netq_create.restype = C.c_int
         L.netq_submit.argtypes = [vp, P(net_desc), P(vp), P(C.c_uint64)]
@@ -266,6 +267,74 @@ class Network:
     def close(self):
         if getattr(self, "h", None):
             lib().net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve_batch(networks, opts: net_opts | None = None, check=True):
+    """net_solve_batch over a list of Network objects; returns [Result]."""
+    L = lib()
+    n = len(networks)
+    hs = (C.c_void_p * n)(*[net.h for net in networks])
+    res = (net_result * n)()
+    st = L.net_solve_batch(hs, n, C.byref(opts) if opts is not None else None, res)
+    if check and st not in (NET_OK, NET_ENOTCONVERGED):
+        raise NetError(st, "net_solve_batch")
+    return [Result.from_c(res[i]) for i in range(n)]
+
+
+class Queue:
+    """netq_*: continuous-batching request queue on the current device."""
+
+    def __init__(self, mem_budget_bytes, max_slots, opts: net_opts | None = None):
+        L = lib()
+        h = C.c_void_p()
+        _check(L.netq_create(int(mem_budget_bytes), int(max_slots),
+                             C.byref(opts) if opts is not None else None, C.byref(h)),
+               "netq_create")
+        self.h = h
+
+    def submit(self, dims, planes, flow_axis=0, p_in=1.0, p_out=0.0):
+        keep, ptrs, bdt, dev, _ = marshal_planes(planes, len(dims))
+        if dev:
+            raise TypeError("queue requests take host (numpy) bond planes")
+        desc = make_desc(dims, flow_axis, p_in, p_out, bdt, 0, None)
+        t = C.c_uint64()
+        _check(lib().netq_submit(self.h, C.byref(desc), ptrs, C.byref(t)), "netq_submit")
+        return t.value
+
+    def poll(self, ticket):
+        r = net_result()
+        st = lib().netq_poll(self.h, C.c_uint64(ticket), C.byref(r))
+        return st, (Result.from_c(r) if st != NET_EBUSY else None)
+
+    def wait(self, ticket, timeout_ms=-1):
+        r = net_result()
+        st = lib().netq_wait(self.h, C.c_uint64(ticket), int(timeout_ms), C.byref(r))
+        return st, (Result.from_c(r) if st != NET_ETIMEOUT else None)
+
+    def cancel(self, ticket):
+        return lib().netq_cancel(self.h, C.c_uint64(ticket))
+
+    def stats(self):
+        p50, p99, n = C.c_double(), C.c_double(), C.c_uint64()
+        _check(lib().netq_stats(self.h, C.byref(p50), C.byref(p99), C.byref(n)), "netq_stats")
+        return p50.value, p99.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().netq_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -27,7 +27,8 @@ def so():
 def test_header_declares_the_abi():
     names = declared_functions()
     for n in ["net_create", "net_solve", "net_flux", "net_get_pressure", "net_get_labels",
-              "net_destroy", "net_last_error"]:
+              "net_destroy", "net_solve_batch", "netq_create", "netq_submit", "netq_poll",
+              "netq_wait", "netq_cancel", "netq_stats", "netq_destroy", "net_last_error"]:
         assert n in names
 
 

@@ -1,0 +1,144 @@
+"""Batched solves (net_solve_batch) and the continuous-batching queue.
+
+Each network's result in a batch or in the queue must equal its stand-alone
+net_solve within the solver's accuracy target (1e-8 relative effective
+conductance) and match the FP64 oracle to the same tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_03301_gb300 import netgen
+
+pytestmark = pytest.mark.gpu
+G_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ns():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1908_03301_gb300 import netsolve
+
+    netsolve.lib(build_if_missing=True)
+    return netsolve
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def mixed_nets(count, seed0=0, with3d=True):
+    nets = []
+    for i in range(count):
+        if with3d and i % 4 == 3:
+            gen = netgen.rng(5000 + seed0 + i)
+            s = int(gen.integers(8, 28))
+            dims = (s, s + 3, s + 1)
+            planes = netgen.lognormal_iid(dims, gen, 1.0)
+            if i % 8 == 7:
+                planes = netgen.percolate(planes, 0.4, gen)
+            nets.append((dims, planes))
+        else:
+            nets.append(netgen.batch_instance(seed0 + i, smin=24, smax=180))
+    return nets
+
+
+def solo(ns, dims, planes, precision=0):
+    with ns.Network(dims, planes) as net:
+        return net.solve(ns.make_opts(precision=precision))
+
+
+def test_batch_matches_solo_and_oracle(ns):
+    specs = mixed_nets(14, seed0=0)
+    nets = [ns.Network(d, p) for d, p in specs]
+    res = ns.solve_batch(nets)
+    for (dims, planes), net, r in zip(specs, nets, res):
+        assert r.status == ns.NET_OK, r
+        s = solo(ns, dims, planes)
+        if s.g_eff == 0.0:
+            assert r.g_eff == 0.0
+            continue
+        assert rel(r.g_eff, s.g_eff) <= G_TOL
+        ref = oracle.solve(dims, planes, tol=1e-13)
+        assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        P = net.pressure()
+        assert np.max(np.abs(P - ref.P)) <= 1e-7
+    for net in nets:
+        net.close()
+
+
+def test_batch_fp64_and_determinism(ns):
+    specs = mixed_nets(8, seed0=40)
+    nets = [ns.Network(d, p) for d, p in specs]
+    r1 = ns.solve_batch(nets, ns.make_opts(precision=ns.NET_FP64))
+    r2 = ns.solve_batch(nets, ns.make_opts(precision=ns.NET_FP64))
+    for (dims, planes), a, b in zip(specs, r1, r2):
+        assert a.status == ns.NET_OK and b.status == ns.NET_OK
+        assert a.g_eff == b.g_eff and a.inner_iters == b.inner_iters
+        ref = oracle.solve(dims, planes, tol=1e-13)
+        if ref.g_eff > 0:
+            assert rel(a.g_eff, ref.g_eff) <= G_TOL
+    m1 = ns.solve_batch(nets)
+    m2 = ns.solve_batch(nets)
+    assert [x.g_eff for x in m1] == [x.g_eff for x in m2]
+    for net in nets:
+        net.close()
+
+
+def test_batch_degenerate_members(ns):
+    dims = (20, 12)
+    gen = netgen.rng(9)
+    cut = netgen.lognormal_iid(dims, gen)
+    cut[0][:, 7] = 0.0  # no spanning cluster
+    uni = netgen.uniform((33, 17), 2.0)
+    specs = [(dims, cut), ((33, 17), uni)] + mixed_nets(3, seed0=70, with3d=False)
+    nets = [ns.Network(d, p) for d, p in specs]
+    res = ns.solve_batch(nets)
+    assert res[0].g_eff == 0.0 and res[0].n_active == 0
+    assert rel(res[1].g_eff, 2.0 * 17 / 32) <= 1e-12
+    for net in nets:
+        net.close()
+    assert ns.solve_batch([]) == []
+
+
+def test_queue_results_match_solo(ns):
+    specs = mixed_nets(12, seed0=100)
+    with ns.Queue(mem_budget_bytes=64 << 20, max_slots=4) as q:
+        tickets = [q.submit(d, p) for d, p in specs]
+        results = [q.wait(t, timeout_ms=120000) for t in tickets]
+        p50, p99, n = q.stats()
+    assert n == len(specs) and 0 < p50 <= p99
+    for (dims, planes), (st, r) in zip(specs, results):
+        assert st == ns.NET_OK, (st, r)
+        s = solo(ns, dims, planes)
+        if s.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, s.g_eff) <= G_TOL
+
+
+def test_queue_budget_cancel_and_errors(ns):
+    with ns.Queue(mem_budget_bytes=8 << 20, max_slots=1) as q:
+        big = netgen.uniform((1024, 1024))
+        with pytest.raises(ns.NetError) as ei:
+            q.submit((1024, 1024), big)
+        assert ei.value.status == ns.NET_EBUDGET
+        bad = netgen.uniform((30, 30))
+        bad[0][3, 4] = -2.0
+        tb = q.submit((30, 30), bad)
+        specs = mixed_nets(6, seed0=200, with3d=False)
+        ts = [q.submit(d, p) for d, p in specs]
+        c = q.cancel(ts[-1])
+        assert c in (ns.NET_OK, ns.NET_EBUSY)
+        st, _ = q.wait(tb, timeout_ms=60000)
+        assert st == ns.NET_EINVAL
+        for t in ts[:-1]:
+            st, r = q.wait(t, timeout_ms=60000)
+            assert st == ns.NET_OK
+        st, _ = q.wait(ts[-1], timeout_ms=60000)
+        assert st == (ns.NET_ECANCELLED if c == ns.NET_OK else ns.NET_OK)
+        # a read ticket is gone
+        st, _ = q.poll(ts[0])
+        assert st == ns.NET_EINVAL
