@@ -43,6 +43,12 @@ def args_():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fbm2048", choices=["fbm2048", "perc3d", "batch", "serve"],
+                    help="fbm2048: the headline 2048^2 solve; perc3d: 256^3 percolation; batch: "
+                         "512 networks in one batched solve; serve: the request queue")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--profile-solve", action="store_true",
                     help="one set-up and one refinement step on the workload, printing the inner "
                          "iteration count (for normalising profiler counters per iteration)")
@@ -359,10 +365,178 @@ def run_profile_solve(a):
                       "inner_ms": r.inner_ms, "n_active": r.n_active}), flush=True)
 
 
+# ---------------------------------------------------------------- other workloads
+def _clocked(fn):
+    with Clocks(0) as clk:
+        out = fn()
+    return out, clk.summary()
+
+
+def run_perc3d(a):
+    """256^3 bond percolation (p = 0.26, FP32 conductances from a 3D FBM):
+    labelling + mixed solve per step, FP64 solve beside it."""
+    import torch
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    dims, planes = netgen.workload_perc3d()
+    dev = torch.device("cuda", 0)
+    tplanes = [torch.from_numpy(g).to(dev) for g in planes]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def steps(precision, k, w):
+        for _ in range(w):
+            with ns.Network(dims, tplanes) as net:
+                net.solve(ns.make_opts(precision=precision, tol_rel=TOL_REL, stream=stream.cuda_stream))
+        ms, res = [], []
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with ns.Network(dims, tplanes) as net:
+                r = net.solve(ns.make_opts(precision=precision, tol_rel=TOL_REL, stream=stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            res.append(r)
+        return ms, res
+
+    (ms, res), clocks = _clocked(lambda: steps(ns.NET_MIXED, a.steps, a.warmup))
+    ms64, res64 = steps(ns.NET_FP64, max(1, a.fp64_steps), 1)
+    r0 = res[-1]
+    N = dims[0] * dims[1] * dims[2]
+    b_act = 44 * r0.n_active
+    b_grid = 44 * N
+    it_s = r0.inner_ms / 1e3 / max(1, r0.inner_iters)
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    ref = stored_oracle("perc256_x")
+    line = {"metric": METRIC, "workload": "perc3d", "value": len(ms) / (sum(ms) / 1e3),
+            "unit": "solves/s", "ms_per_step": statistics.mean(ms), "p50_ms": statistics.median(ms),
+            "steps": len(ms), "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "3D 256^3 bond percolation p=0.26, FBM H=0.3 sigma=1, FP32 "
+                                   "conductances", "nodes": N, "n_active": r0.n_active,
+                       "tol_rel": TOL_REL},
+            "accuracy": {"g_eff": r0.g_eff, "g_eff_fp64": res64[-1].g_eff,
+                         "rel_mixed_vs_fp64": abs(r0.g_eff - res64[-1].g_eff) / max(abs(res64[-1].g_eff), 1e-300),
+                         "rel_err_vs_oracle": (abs(r0.g_eff - ref["g_eff"]) / ref["g_eff"]) if ref else None,
+                         "outer_iters": r0.outer_iters, "inner_iters": r0.inner_iters,
+                         "fp64_fallback": r0.fp64_fallback},
+            "fp64_cg": {"value": len(ms64) / (sum(ms64) / 1e3), "unit": "solves/s",
+                        "ms_per_step": statistics.mean(ms64), "inner_iters": res64[-1].inner_iters},
+            "inner": {"us_per_iteration": it_s * 1e6,
+                      "active_gbs": b_act / it_s / 1e9, "grid_gbs": b_grid / it_s / 1e9,
+                      "frac_active": b_act / it_s / 1e9 / peak, "frac_grid": b_grid / it_s / 1e9 / peak},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(a):
+    """512 independent 2D networks (sides 64..1024, lognormal sigma=1, even
+    ones percolated at p=0.55) created and solved together per step."""
+    import torch
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    specs = [netgen.batch_instance(i) for i in range(a.batch_count)]
+    dev = torch.device("cuda", 0)
+    tpl = [[torch.from_numpy(g).to(dev) for g in planes] for _, planes in specs]
+    nodes = sum(d[0] * d[1] for d, _ in specs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one():
+        nets = [ns.Network(d, t) for (d, _), t in zip(specs, tpl)]
+        res = ns.solve_batch(nets, ns.make_opts(tol_rel=TOL_REL))
+        for n in nets:
+            n.close()
+        return res
+
+    for _ in range(a.warmup):
+        one()
+    times, res = [], None
+    with Clocks(0) as clk:
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            res = one()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+    clocks = clk.summary()
+    ui = sum(r.inner_iters * r.n_active for r in res)
+    ok = sum(r.status == 0 for r in res)
+    lat = sorted(r.ms for r in res)
+    line = {"metric": METRIC, "workload": "batch", "value": a.batch_count * len(times) / sum(times),
+            "unit": "solves/s", "ms_per_step": statistics.mean(times) * 1e3, "steps": len(times),
+            "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{a.batch_count} 2D networks, sides U{{64..1024}}, lognormal "
+                                   "sigma=1, even ones percolated p=0.55; created + net_solve_batch",
+                       "nodes": nodes, "tol_rel": TOL_REL},
+            "converged": ok, "unknown_iterations_per_s": ui / statistics.mean(times),
+            "algorithmic_gbs": 40 * ui / statistics.mean(times) / 1e9,
+            "per_network_ms_p50": lat[len(lat) // 2], "per_network_ms_p99": lat[int(0.99 * (len(lat) - 1))],
+            "fp64_fallbacks": sum(r.fp64_fallback for r in res), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a):
+    """Poisson request stream of mixed networks (70 % 2D sides 32..1024, 30 %
+    3D sides 16..128; FBM or lognormal; 20 % near-critical percolation)
+    through the queue with a 150 GB budget.  A pool of distinct requests is
+    generated up front and cycled; the offered rate is --serve-rate, then a
+    sweep at 0.25 / 0.5 / 0.8 of the measured capacity."""
+    import threading
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    pool = [netgen.request_instance(i) for i in range(48)]
+
+    def run(rate, n):
+        arr = netgen.poisson_arrivals(n, rate)
+        with ns.Queue(mem_budget_bytes=150 << 30, max_slots=256, opts=ns.make_opts(tol_rel=TOL_REL)) as q:
+            tickets = []
+            t0 = time.perf_counter()
+            for i in range(n):
+                dt = arr[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                d, pl = pool[i % len(pool)]
+                tickets.append(q.submit(d, pl))
+            results = [q.wait(t, timeout_ms=600000) for t in tickets]
+            t1 = time.perf_counter()
+            p50, p99, done = q.stats()
+        ok = sum(st == 0 for st, _ in results)
+        return {"offered_rate": rate, "requests": n, "ok": ok, "solves_per_s": n / (t1 - t0),
+                "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0}
+
+    run(50.0, 16)  # warm-up
+    sat = run(a.serve_rate, a.serve_requests)
+    cap = sat["solves_per_s"]
+    sweep = [run(f * cap, max(32, a.serve_requests // 2)) for f in (0.25, 0.5, 0.8)]
+    line = {"metric": METRIC, "workload": "serve", "value": sat["solves_per_s"], "unit": "solves/s",
+            "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"], "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "Poisson stream, 70% 2D (32..1024) / 30% 3D (16..128), FBM or "
+                                   "lognormal, 20% near-critical percolation, 150 GB budget; a pool "
+                                   "of 48 distinct requests cycled",
+                       "tol_rel": TOL_REL},
+            "saturated": sat, "sweep": sweep}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.profile_solve:
         run_profile_solve(a)
+        return
+    if a.workload != "fbm2048" and a.impl == "ours":
+        {"perc3d": run_perc3d, "batch": run_batch, "serve": run_serve}[a.workload](a)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -97,8 +97,8 @@ typedef struct {
 /* Solver options.  net_opts_default() fills the defaults listed here. */
 typedef struct {
     int precision;           /* NET_MIXED (default) or NET_FP64 */
-    double tol_rel;          /* outer stop: ||b - G P||_2 <= tol_rel ||b||_2;
-                                default 1e-11 */
+    double tol_rel;          /* outer stop: ||b - G P||_2 <= tol_rel ||b||_2
+                                (and see tol_geff); default 1e-11 */
     double tol_inner;        /* inner relative reduction per refinement step
                                 (mixed); default 1e-4 */
     int max_outer;           /* refinement steps; default 40 */
@@ -110,6 +110,13 @@ typedef struct {
                                 linear profile along the flow axis */
     int x0_on_device;        /* x0 is a device pointer */
     void *stream;            /* cudaStream_t to run on; NULL = network's own */
+    double tol_geff;         /* outer stop also needs the estimated relative
+                                error of g_eff below this; default 1e-9.  The
+                                estimate is first order: by the symmetry of
+                                Eq. 3, Q_in's sensitivity to the nodal
+                                residual r is the pressure field scaled to
+                                (p_in, p_out) = (1, 0), so the error of Q_in is
+                                sum_i (P_i - p_out) r_i / (p_in - p_out). */
 } net_opts;
 
 /* Per-solve result and diagnostics. */
@@ -128,6 +135,7 @@ typedef struct {
     float inner_ms;          /* device time spent in the inner CG loop */
     int64_t inner_launches;  /* inner CG kernel launches (incl. no-op tails) */
     net_status status;
+    double g_eff_err;        /* estimated relative error of g_eff (see tol_geff) */
 } net_result;
 
 /* Fill *opts with the defaults listed in net_opts. */

@@ -27,6 +27,8 @@ __global__ void gather_status_kernel(const InnerScal *const *s, int n, int *stop
 
 __global__ void set_stop_kernel(InnerScal *s, int v) { s->stop = v; }
 
+__global__ void retire_kernel(SweepInst *inst, int idx, InnerScal *dead) { inst[idx].s = dead; }
+
 #define CKB(call)                                                \
     do {                                                         \
         cudaError_t e_ = (call);                                 \
@@ -56,6 +58,19 @@ BatchEngine::BatchEngine(int device, cudaStream_t stream) : device_(device), st_
             groups_[d][f].ndim = d + 2;
             groups_[d][f].f32 = f;
         }
+    InnerScal dead{};
+    dead.stop = 1;
+    if (cudaMallocAsync((void **)&dead_, sizeof(InnerScal), st_) == cudaSuccess)
+        cudaMemcpyAsync(dead_, &dead, sizeof(InnerScal), cudaMemcpyHostToDevice, st_);
+    cudaStreamSynchronize(st_);
+}
+
+void BatchEngine::retire(Group &g, BatchItem *it) {
+    for (size_t k = 0; k < g.planned.size(); k++)
+        if (g.planned[k] == it) {
+            retire_kernel<<<1, 1, 0, st_>>>(g.d_inst, (int)k, dead_);
+            g.planned[k] = nullptr;
+        }
 }
 
 BatchEngine::~BatchEngine() {
@@ -71,6 +86,7 @@ BatchEngine::~BatchEngine() {
     dfree((void *)d_sptr_, st_);
     dfree(d_stop_, st_);
     dfree(d_iter_, st_);
+    dfree(dead_, st_);
     cudaStreamSynchronize(st_);
 }
 
@@ -102,6 +118,7 @@ void BatchEngine::finish(BatchItem *it, net_status st) {
     r.outer_iters = it->outer;
     r.inner_iters = it->inner_total;
     r.fp64_fallback = it->fallback;
+    r.g_eff_err = geff_err(n);
     r.ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - it->t_start).count();
     r.status = st;
     n->last = r;
@@ -109,6 +126,8 @@ void BatchEngine::finish(BatchItem *it, net_status st) {
     // no more sweeps for this network, whatever plan it is still part of
     set_stop_kernel<<<1, 1, 0, st_>>>(&n->dsc->in[0], 1);
     set_stop_kernel<<<1, 1, 0, st_>>>(&n->dsc->in[1], 1);
+    for (int d = 0; d < 2; d++)
+        for (int f = 0; f < 2; f++) retire(groups_[d][f], it);
     it->done = true;
     done_.push_back(it);
 }
@@ -152,8 +171,8 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
     for (BatchItem *it : ok) {
         net_t *n = it->net;
         it->rel = n->bnorm > 0.0 ? std::sqrt(n->hsc->os.rr) / n->bnorm : 0.0;
-        it->rel_prev = it->rel;
-        if (n->bnorm == 0.0 || it->rel <= it->opts.tol_rel) {
+        it->rel_prev = outer_dist(n, it->opts, it->rel);
+        if (n->bnorm == 0.0 || it->rel_prev <= 1.0) {
             finish(it, NET_OK);
             continue;
         }
@@ -227,6 +246,7 @@ net_status BatchEngine::rebuild(Group &g, int K) {
     g.grid = hp.grid;
     g.K = K;
     g.dirty = false;
+    g.planned = g.items;
     return NET_OK;
 }
 
@@ -290,14 +310,16 @@ net_status BatchEngine::step(int K) {
     for (BatchItem *it : stopped) {
         net_t *nt = it->net;
         it->outer++;
-        it->rel_prev = it->rel;
+        const double dist_prev = it->rel_prev;
         it->rel = std::sqrt(nt->hsc->os.rr) / nt->bnorm;
-        if (it->rel <= it->opts.tol_rel) {
+        const double dist = outer_dist(nt, it->opts, it->rel);
+        it->rel_prev = dist;
+        if (dist <= 1.0) {
             finish(it, NET_OK);
         } else if (it->outer >= it->opts.max_outer) {
             set_error("batch: not converged after %d refinement steps", it->outer);
             finish(it, NET_ENOTCONVERGED);
-        } else if (it->f32 && it->rel > 0.5 * it->rel_prev) {
+        } else if (it->f32 && dist > 0.5 * dist_prev) {
             to_fp64.push_back(it);
         }
     }
@@ -309,6 +331,7 @@ net_status BatchEngine::step(int K) {
         if (s != NET_OK) return s;
         Group &g32 = group_of(nt->g.ndim, 1);
         g32.items.erase(std::remove(g32.items.begin(), g32.items.end(), it), g32.items.end());
+        retire(g32, it);
         g32.dirty = true;
         it->f32 = 0;
         it->fallback = 1;

@@ -23,7 +23,8 @@ struct BatchItem {
     int f32 = 1;             // inner precision in use
     int outer = 0;
     long long inner_total = 0;
-    double rel = 0.0, rel_prev = 0.0;
+    double rel = 0.0;
+    double rel_prev = 0.0;   // outer stopping measure after the last pass
     int fallback = 0;
     bool done = false;
     net_result res{};
@@ -57,7 +58,13 @@ private:
         size_t cap_inst = 0, cap_segs = 0, cap_part = 0;
         int grid = 0, K = 0;
         cudaGraphExec_t exec = nullptr;
+        std::vector<BatchItem *> planned;  // item order of d_inst
     };
+    // A network leaving a group (finished or moved) must not be read by that
+    // group's current plan again: its record is pointed at dead_ (stop = 1),
+    // so the sweep skips it even if its memory is released before the next
+    // replan.
+    void retire(Group &g, BatchItem *it);
     net_status rebuild(Group &g, int K);
     net_status outer_pass(BatchItem *it, int apply_corr, int corr_f32);
     void finish(BatchItem *it, net_status st);
@@ -74,6 +81,7 @@ private:
     int *d_stop_ = nullptr;
     long long *d_iter_ = nullptr;
     size_t cap_g_ = 0;
+    InnerScal *dead_ = nullptr;  // always-stopped scalars
 };
 
 }  // namespace netsolve

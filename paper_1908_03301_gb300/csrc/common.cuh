@@ -70,6 +70,7 @@ struct OuterScal {
     double rmax;     // max |r_i|
     double rh2;      // sum (D^-1/2 r)_i^2
     double qin, qout, energy;
+    double ez;       // sum (x_i - p_out) r_i: first-order error of Q_in
     unsigned int counter;
 };
 

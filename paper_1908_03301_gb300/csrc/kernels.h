@@ -89,6 +89,7 @@ struct OuterArgs {
     InnerScal *is;        // inner scalars to arm for the next inner solve
     double tol_floor;     // smallest relative reduction asked of the inner solve
     double tol_rel;       // outer tolerance (relative 2-norm residual)
+    double tol_geff;      // outer tolerance on the estimated relative error of G_eff
     double bnorm;         // ||b||_2
     long long max_inner, stag_window;
     double *partials;

@@ -265,8 +265,8 @@ __global__ void __launch_bounds__(NT)
 outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
              const GT *__restrict__ g2, const double *__restrict__ dis, const double *__restrict__ x,
              TI *__restrict__ r_out, OuterScal *os,
-             InnerScal *is, double tol_floor, double tol_rel, double bnorm, long long max_inner,
-             long long stag_window, double *partials) {
+             InnerScal *is, double tol_floor, double tol_rel, double tol_geff, double bnorm,
+             long long max_inner, long long stag_window, double *partials) {
     using OT = OTile<NDIM>;
     constexpr int TW = OT::TW, TH = OT::TH, TD = OT::TD;
     __shared__ double sx[OT::ZP * OT::SH * OT::SW];
@@ -286,7 +286,7 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     }
     __syncthreads();
 
-    double rr = 0.0, rmax = 0.0, rh2 = 0.0, qin = 0.0, qout = 0.0, en = 0.0;
+    double rr = 0.0, rmax = 0.0, rh2 = 0.0, qin = 0.0, qout = 0.0, en = 0.0, ez = 0.0;
     for (int c = threadIdx.x; c < TW * TH * TD; c += NT) {
         const int xx = c % TW, t = c / TW, yy = t % TH, zz = t / TH;
         const int cx = x0 + xx, cy = y0 + yy, cz = z0 + zz;
@@ -312,12 +312,13 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
         rr += rv * rv;
         rmax = fmax(rmax, fabs(rv));
         rh2 += rh * rh;
+        ez += (xi - g.p_out) * rv;
         if (cf == 1) qin += (double)gp[g.f][i - g.stride(g.f)] * (g.p_in - xi);
         if (cf == g.nf - 2) qout += (double)gp[g.f][i] * (xi - g.p_out);
     }
-    double v[6] = {rr, rmax, rh2, qin, qout, en};
-    const int ops[6] = {RED_SUM, RED_MAX, RED_SUM, RED_SUM, RED_SUM, RED_SUM};
-    if (!grid_reduce<6, NT>(v, ops, partials, &os->counter)) return;
+    double v[7] = {rr, rmax, rh2, qin, qout, en, ez};
+    const int ops[7] = {RED_SUM, RED_MAX, RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_SUM};
+    if (!grid_reduce<7, NT>(v, ops, partials, &os->counter)) return;
     if (threadIdx.x != 0) return;
     os->rr = v[0];
     os->rmax = v[1];
@@ -325,14 +326,26 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     os->qin = v[3];
     os->qout = v[4];
     os->energy = v[5];
+    os->ez = v[6];
     is->alpha = 0.0;
     is->beta = 0.0;
     is->rho0 = v[2];
     is->rho = v[2];
-    // inner target: reach the outer tolerance in this step if possible, but
-    // never ask the inner loop for more than tol_floor (its precision limit)
+    // Stop when the relative residual is below tol_rel and the first-order
+    // error of G_eff is below tol_geff.  By the symmetry of Eq. 3 the
+    // sensitivity of Q_in to the nodal residual r is the pressure field
+    // normalised to (p_in, p_out) = (1, 0), so Q_in(x) - Q_in(exact) is
+    // sum_i (x_i - p_out) r_i / dP to first order.
+    // Inner target: reach both in this step if possible, but never ask the
+    // inner loop for more than tol_floor (its precision limit).
+    const double dP = g.p_in - g.p_out;
     const double rel = bnorm > 0.0 ? sqrt(v[0]) / bnorm : 0.0;
-    double t = 0.5 * tol_rel / fmax(rel, 1e-300);
+    const double G = v[3] / dP;
+    const double gerr = G != 0.0 ? fabs(v[6]) / (dP * dP) / fabs(G) : 0.0;
+    const bool done = !(rel > tol_rel) && !(gerr > tol_geff);
+    double t = 1.0;
+    if (rel > 0.0) t = fmin(t, 0.5 * tol_rel / rel);
+    if (gerr > 0.0) t = fmin(t, 0.5 * tol_geff / gerr);
     t = fmin(0.5, fmax(t, tol_floor));
     is->tol2 = t * t;
     is->best = v[2];
@@ -342,8 +355,8 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     is->stag_window = stag_window;
     is->err = 0;
     is->counter = 0u;
-    // no inner solve when the outer tolerance is met (or nothing to solve)
-    is->stop = (v[2] > 0.0 && !(rel <= tol_rel)) ? 0 : 1;
+    // no inner solve when the outer tolerances are met (or nothing to solve)
+    is->stop = (v[2] > 0.0 && !done) ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -383,7 +396,7 @@ template <typename GT, typename TI, int NDIM>
 cudaError_t launch_outer_t(const OuterArgs &a, cudaStream_t st) {
     outer_kernel<GT, TI, NDIM><<<outer_grid<NDIM>(a.g), NT, 0, st>>>(
         a.g, (const GT *)a.graw[0], (const GT *)a.graw[1], (const GT *)a.graw[2], a.dis, a.x,
-        (TI *)a.r_out, a.os, a.is, a.tol_floor, a.tol_rel, a.bnorm, a.max_inner,
+        (TI *)a.r_out, a.os, a.is, a.tol_floor, a.tol_rel, a.tol_geff, a.bnorm, a.max_inner,
         a.stag_window, a.partials);
     return cudaGetLastError();
 }

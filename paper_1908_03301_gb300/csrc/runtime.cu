@@ -283,6 +283,7 @@ OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_
     o.is = &n->dsc->in[k];
     o.tol_floor = f32 ? op.tol_inner : 0.0;
     o.tol_rel = op.tol_rel;
+    o.tol_geff = op.tol_geff > 0.0 ? op.tol_geff : 1e-9;
     o.bnorm = n->bnorm;
     o.max_inner = op.max_inner;
     o.stag_window = std::max(400LL, 8LL * std::max(n->g.nx, std::max(n->g.ny, n->g.nz)));
@@ -459,14 +460,15 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     CK(cudaStreamSynchronize(st));
     const double bn = n->bnorm;
     double rel = bn > 0.0 ? std::sqrt(n->hsc->os.rr) / bn : 0.0;
+    double dist = outer_dist(n, o, rel);
     int outer = 0;
     long long inner_total = 0, launches = 0;
     float inner_ms = 0.f;
     int fallback = 0;
     net_status status = NET_OK;
-    double rel_prev = rel;
+    double dist_prev = dist;
     while (true) {
-        if (rel <= o.tol_rel || bn == 0.0) break;
+        if (dist <= 1.0 || bn == 0.0) break;
         if (outer >= o.max_outer) { status = NET_ENOTCONVERGED; break; }
         CK(cudaEventRecord(n->ev[1], st));
         long long chunks = 0;
@@ -543,8 +545,9 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rel = std::sqrt(n->hsc->os.rr) / bn;
+        dist = outer_dist(n, o, rel);
         // a refinement step that gains less than 2x: continue in FP64
-        if (f32 && rel > o.tol_rel && rel > 0.5 * rel_prev) {
+        if (f32 && dist > 1.0 && dist > 0.5 * dist_prev) {
             f32 = 0;
             fallback = 1;
             s = ensure_precision(n, 0, st);
@@ -559,8 +562,9 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             rel = std::sqrt(n->hsc->os.rr) / bn;
+            dist = outer_dist(n, o, rel);
         }
-        rel_prev = rel;
+        dist_prev = dist;
     }
     CK(cudaEventRecord(n->ev[2], st));
     CK(cudaEventSynchronize(n->ev[2]));
@@ -585,6 +589,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     r->ms = total_ms;
     r->inner_ms = inner_ms;
     r->inner_launches = launches;
+    r->g_eff_err = geff_err(n);
     r->status = status;
     n->last = *r;
     n->solved = true;
@@ -608,6 +613,7 @@ NET_API void net_opts_default(net_opts *o) {
     o->max_outer = 40;
     o->max_inner = 200000;
     o->check_every = 0;
+    o->tol_geff = 1e-9;
 }
 
 NET_API net_status net_create(const net_desc *desc, const void *const g[3], net_t **out) {

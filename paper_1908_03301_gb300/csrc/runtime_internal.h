@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "../../include/netsolve.h"
 #include "kernels.h"
 #include "sweep.cuh"
@@ -72,6 +74,18 @@ inline cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
 }
 inline void dfree(void *p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
+}
+// Outer stopping measure: max(rel / tol_rel, g_err / tol_geff); converged
+// when <= 1.  g_err is the first-order relative error of G_eff estimated by
+// the last outer pass (see net_opts.tol_geff).
+inline double eff_tol_geff(const net_opts &o) { return o.tol_geff > 0.0 ? o.tol_geff : 1e-9; }
+inline double geff_err(const net_t *n) {
+    const double dP = n->g.p_in - n->g.p_out;
+    const double G = n->hsc->os.qin / dP;
+    return G != 0.0 ? std::fabs(n->hsc->os.ez) / (dP * dP) / std::fabs(G) : 0.0;
+}
+inline double outer_dist(const net_t *n, const net_opts &o, double rel) {
+    return std::fmax(rel / o.tol_rel, geff_err(n) / eff_tol_geff(o));
 }
 // Scaled bonds and inner vectors of one precision (allocated on first use).
 net_status ensure_precision(net_t *n, int f32, cudaStream_t st);

@@ -32,7 +32,8 @@ class net_desc(C.Structure):
 class net_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol_rel", C.c_double), ("tol_inner", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int64), ("check_every", C.c_int),
-                ("x0", C.c_void_p), ("x0_on_device", C.c_int), ("stream", C.c_void_p)]
+                ("x0", C.c_void_p), ("x0_on_device", C.c_int), ("stream", C.c_void_p),
+                ("tol_geff", C.c_double)]
 
 
 class net_result(C.Structure):
@@ -41,7 +42,7 @@ class net_result(C.Structure):
                 ("max_imbalance", C.c_double), ("energy_g", C.c_double),
                 ("n_active", C.c_int64), ("outer_iters", C.c_int), ("inner_iters", C.c_int64),
                 ("fp64_fallback", C.c_int), ("ms", C.c_float), ("inner_ms", C.c_float),
-                ("inner_launches", C.c_int64), ("status", C.c_int)]
+                ("inner_launches", C.c_int64), ("status", C.c_int), ("g_eff_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,8 +127,10 @@ def opts_default() -> net_opts:
 
 
 def make_opts(precision=NET_MIXED, tol_rel=None, tol_inner=None, max_outer=None,
-              max_inner=None, check_every=None, stream=None) -> net_opts:
+              max_inner=None, check_every=None, stream=None, tol_geff=None) -> net_opts:
     o = opts_default()
+    if tol_geff is not None:
+        o.tol_geff = tol_geff
     o.precision = precision
     if tol_rel is not None:
         o.tol_rel = tol_rel
@@ -203,6 +206,7 @@ class Result:
     inner_ms: float
     inner_launches: int
     status: int
+    g_eff_err: float
 
     @classmethod
     def from_c(cls, r: net_result):

@@ -104,8 +104,10 @@ def test_batch_degenerate_members(ns):
 
 
 def test_queue_results_match_solo(ns):
-    specs = mixed_nets(12, seed0=100)
-    with ns.Queue(mem_budget_bytes=64 << 20, max_slots=4) as q:
+    """Requests finish at different steps and their networks are released at
+    once while others keep running (30 requests, 6 slots, 2D and 3D)."""
+    specs = mixed_nets(30, seed0=100)
+    with ns.Queue(mem_budget_bytes=96 << 20, max_slots=6) as q:
         tickets = [q.submit(d, p) for d, p in specs]
         results = [q.wait(t, timeout_ms=120000) for t in tickets]
         p50, p99, n = q.stats()

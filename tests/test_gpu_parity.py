@@ -214,3 +214,18 @@ def test_invariants_after_solve(ns):
     imb = oracle.residual(dims, planes, P)
     assert np.max(np.abs(imb)) <= 1e-8 * max(np.max(g) for g in planes)
     assert abs(np.max(np.abs(imb)) - r.max_imbalance) <= 1e-12 + 1e-6 * r.max_imbalance
+
+
+@pytest.mark.parametrize("tol_rel", [1e-6, 1e-8])
+def test_geff_error_estimate_tracks_actual_error(ns, tol_rel):
+    """The reported g_eff_err (first-order adjoint estimate) matches the
+    actual relative error against the oracle when the solve stops early."""
+    dims = (160, 120)
+    gen = netgen.rng(31)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen, 1.5), 0.7, gen)
+    ref = oracle.solve(dims, planes, tol=1e-14)
+    with ns.Network(dims, planes) as net:
+        r = net.solve(ns.make_opts(precision=ns.NET_FP64, tol_rel=tol_rel, tol_geff=1.0))
+    actual = rel(r.g_eff, ref.g_eff)
+    assert actual > 1e-13  # the early stop left a measurable error
+    assert 0.8 <= r.g_eff_err / actual <= 1.25, (r.g_eff_err, actual)
