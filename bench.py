@@ -513,8 +513,13 @@ def run_serve(a):
             t1 = time.perf_counter()
             p50, p99, done = q.stats()
         ok = sum(st == 0 for st, _ in results)
-        return {"offered_rate": rate, "requests": n, "ok": ok, "solves_per_s": n / (t1 - t0),
-                "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0}
+        counts = {}
+        for st, _ in results:
+            name = ns.STATUS_NAMES[st] if 0 <= st < len(ns.STATUS_NAMES) else str(st)
+            counts[name] = counts.get(name, 0) + 1
+        errors = sorted({r.error for st, r in results if st != 0 and r is not None})[:4]
+        return {"offered_rate": rate, "requests": n, "ok": ok, "status_counts": counts, "errors": errors,
+                "solves_per_s": n / (t1 - t0), "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0}
 
     run(50.0, 16)  # warm-up
     sat = run(a.serve_rate, a.serve_requests)

@@ -121,6 +121,7 @@ void BatchEngine::finish(BatchItem *it, net_status st) {
     r.g_eff_err = geff_err(n);
     r.ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - it->t_start).count();
     r.status = st;
+    if (st != NET_OK) it->err = last_error();
     n->last = r;
     n->solved = true;
     // no more sweeps for this network, whatever plan it is still part of
@@ -150,6 +151,7 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
         net_t *n = it->net;
         if (!n || n->device != device_) {
             set_error("batch: network is not on the engine's device");
+            it->err = last_error();
             it->res.status = NET_EINVAL;
             it->done = true;
             done_.push_back(it);
@@ -171,8 +173,8 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
     for (BatchItem *it : ok) {
         net_t *n = it->net;
         it->rel = n->bnorm > 0.0 ? std::sqrt(n->hsc->os.rr) / n->bnorm : 0.0;
-        it->rel_prev = outer_dist(n, it->opts, it->rel);
-        if (n->bnorm == 0.0 || it->rel_prev <= 1.0) {
+        it->rel_prev = it->rel;
+        if (n->bnorm == 0.0 || outer_dist(n, it->opts, it->rel) <= 1.0) {
             finish(it, NET_OK);
             continue;
         }
@@ -291,6 +293,7 @@ net_status BatchEngine::step(int K) {
     CKB(cudaStreamSynchronize(st_));
     // outer passes of every network whose inner solve stopped
     std::vector<BatchItem *> stopped;
+    std::vector<int> stop_code, stop_iter;
     for (size_t i = 0; i < n; i++) {
         if (!stop[i]) continue;
         BatchItem *it = run[i];
@@ -304,27 +307,31 @@ net_status BatchEngine::step(int K) {
         if (s != NET_OK) return s;
         CKB(cudaMemcpyAsync(&it->net->hsc->os, &it->net->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st_));
         stopped.push_back(it);
+        stop_code.push_back(stop[i]);
+        stop_iter.push_back((int)iters[i]);
     }
     CKB(cudaStreamSynchronize(st_));
     std::vector<BatchItem *> to_fp64;
-    for (BatchItem *it : stopped) {
+    for (size_t j = 0; j < stopped.size(); j++) {
+        BatchItem *it = stopped[j];
         net_t *nt = it->net;
         it->outer++;
-        const double dist_prev = it->rel_prev;
+        const double rel_prev = it->rel_prev;
         it->rel = std::sqrt(nt->hsc->os.rr) / nt->bnorm;
         const double dist = outer_dist(nt, it->opts, it->rel);
-        it->rel_prev = dist;
+        it->rel_prev = it->rel;
+        trace_outer(nt, "batch", it->outer, it->f32, stop_code[j], stop_iter[j], it->rel);
         if (dist <= 1.0) {
             finish(it, NET_OK);
         } else if (it->outer >= it->opts.max_outer) {
             set_error("batch: not converged after %d refinement steps", it->outer);
             finish(it, NET_ENOTCONVERGED);
-        } else if (it->f32 && dist > 0.5 * dist_prev) {
+        } else if (it->f32 && it->rel > 0.5 * rel_prev) {
             to_fp64.push_back(it);
         }
     }
     for (BatchItem *it : to_fp64) {
-        // a refinement step that gained less than 2x: continue in FP64
+        // an FP32 refinement step that did not halve the residual: continue in FP64
         net_t *nt = it->net;
         set_stop_kernel<<<1, 1, 0, st_>>>(&nt->dsc->in[0], 1);
         net_status s = ensure_precision(nt, 0, st_);

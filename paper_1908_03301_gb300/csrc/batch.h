@@ -11,6 +11,7 @@
 #pragma once
 #include <chrono>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "runtime_internal.h"
@@ -24,10 +25,11 @@ struct BatchItem {
     int outer = 0;
     long long inner_total = 0;
     double rel = 0.0;
-    double rel_prev = 0.0;   // outer stopping measure after the last pass
+    double rel_prev = 0.0;   // relative residual before the last refinement step
     int fallback = 0;
     bool done = false;
     net_result res{};
+    std::string err;         // message of a non-OK finish
     uint64_t user = 0;       // caller's tag (queue ticket)
     std::chrono::steady_clock::time_point t_start;
 };

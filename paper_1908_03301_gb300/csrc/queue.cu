@@ -16,6 +16,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -37,6 +38,7 @@ struct Req {
     size_t foot = 0;
     int state = Q_QUEUED;
     net_result res{};
+    std::string err;  // error message of a request that ended non-OK
     BatchItem item;
     net_t *net = nullptr;
     std::chrono::steady_clock::time_point t_submit;
@@ -65,6 +67,7 @@ namespace {
 
 void finalize_locked(netq_t *q, Req *r, net_status st) {
     r->res.status = st;
+    if (st != NET_OK && r->err.empty()) r->err = last_error();
     r->state = Q_DONE;
     q->lat_ms.push_back(
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count());
@@ -127,7 +130,12 @@ void worker_main(netq_t *q) {
         if (es != NET_OK) {
             // the device failed: every running request ends with that status
             for (Req *r : active)
-                if (!r->item.done) done.push_back(&r->item), r->item.res.status = es, r->item.done = true;
+                if (!r->item.done) {
+                    r->item.res.status = es;
+                    r->item.err = last_error();
+                    r->item.done = true;
+                    done.push_back(&r->item);
+                }
         }
         if (done.empty()) continue;
         std::lock_guard<std::mutex> lk(q->mu);
@@ -136,6 +144,7 @@ void worker_main(netq_t *q) {
             if (f == q->all.end()) continue;
             Req *r = f->second;
             r->res = it->res;
+            r->err = it->err;
             net_destroy(r->net);
             r->net = nullptr;
             finalize_locked(q, r, it->res.status);
@@ -153,6 +162,7 @@ void worker_main(netq_t *q) {
         if (r->net) net_destroy(r->net);
         r->net = nullptr;
         r->res = net_result{};
+        r->err = "queue destroyed while the request was running";
         finalize_locked(q, r, NET_ECANCELLED);
     }
     q->cv_done.notify_all();
@@ -256,6 +266,7 @@ NET_API net_status netq_poll(netq_t *q, uint64_t ticket, net_result *out) {
     if (r->state != Q_DONE) return NET_EBUSY;
     if (out) *out = r->res;
     const net_status st = r->res.status;
+    if (st != NET_OK) set_error("request %llu: %s", (unsigned long long)ticket, r->err.c_str());
     q->all.erase(f);
     delete r;
     return st;
@@ -281,6 +292,7 @@ NET_API net_status netq_wait(netq_t *q, uint64_t ticket, int timeout_ms, net_res
     Req *r = f->second;
     if (out) *out = r->res;
     const net_status st = r->res.status;
+    if (st != NET_OK) set_error("request %llu: %s", (unsigned long long)ticket, r->err.c_str());
     q->all.erase(f);
     delete r;
     return st;
@@ -303,6 +315,7 @@ NET_API net_status netq_cancel(netq_t *q, uint64_t ticket) {
     q->pending.erase(std::remove(q->pending.begin(), q->pending.end(), r), q->pending.end());
     r->res = net_result{};
     r->res.status = NET_ECANCELLED;
+    r->err = "cancelled before it started";
     r->state = Q_DONE;
     q->cv_done.notify_all();
     return NET_OK;
@@ -338,6 +351,7 @@ NET_API net_status netq_destroy(netq_t *q) {
         for (Req *r : q->pending) {
             r->res = net_result{};
             r->res.status = NET_ECANCELLED;
+            r->err = "queue destroyed before the request started";
             r->state = Q_DONE;
         }
         q->pending.clear();

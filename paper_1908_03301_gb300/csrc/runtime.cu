@@ -42,6 +42,15 @@ void set_error(const char *fmt, ...) {
 
 const char *last_error() { return g_err.c_str(); }
 
+void trace_outer(const net_t *n, const char *who, int outer, int f32, int stop, long long iters,
+                 double rel) {
+    static const bool on = getenv("NETSOLVE_TRACE") != nullptr;
+    if (!on) return;
+    fprintf(stderr, "[trace %s %p %lldx%lldx%lld] step %d %s stop %d iters %lld rel %.3e gerr %.3e\n", who,
+            (const void *)n, (long long)n->g.nx, (long long)n->g.ny, (long long)n->g.nz, outer,
+            f32 ? "f32" : "f64", stop, iters, rel, geff_err(n));
+}
+
 net_status cuda_fail(cudaError_t e, const char *what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
     return NET_ECUDA;
@@ -286,7 +295,13 @@ OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_
     o.tol_geff = op.tol_geff > 0.0 ? op.tol_geff : 1e-9;
     o.bnorm = n->bnorm;
     o.max_inner = op.max_inner;
-    o.stag_window = std::max(400LL, 8LL * std::max(n->g.nx, std::max(n->g.ny, n->g.nz)));
+    // An FP32 inner loop that has not halved its residual norm for this many
+    // iterations restarts from a fresh FP64 residual.  FP64 CG has no
+    // precision floor at these targets, and on near-critical networks its
+    // residual plateaus for hundreds of iterations between drops; a restart
+    // there throws away the Krylov space, so its window is much longer.
+    const long long side = std::max(n->g.nx, std::max(n->g.ny, n->g.nz));
+    o.stag_window = f32 ? std::max(400LL, 8LL * side) : std::max(4000LL, 64LL * side);
     o.partials = n->partials;
     return o;
 }
@@ -466,7 +481,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     float inner_ms = 0.f;
     int fallback = 0;
     net_status status = NET_OK;
-    double dist_prev = dist;
+    double rel_prev = rel;
     while (true) {
         if (dist <= 1.0 || bn == 0.0) break;
         if (outer >= o.max_outer) { status = NET_ENOTCONVERGED; break; }
@@ -546,8 +561,11 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         CK(cudaStreamSynchronize(st));
         rel = std::sqrt(n->hsc->os.rr) / bn;
         dist = outer_dist(n, o, rel);
-        // a refinement step that gains less than 2x: continue in FP64
-        if (f32 && dist > 1.0 && dist > 0.5 * dist_prev) {
+        trace_outer(n, "solve", outer, f32, hs->stop, hs->iter, rel);
+        // An FP32 refinement step that did not halve the residual has met
+        // the FP32 limit: continue in FP64.  (The G_eff error estimate is
+        // not monotone under CG and is not used for this decision.)
+        if (f32 && dist > 1.0 && rel > 0.5 * rel_prev) {
             f32 = 0;
             fallback = 1;
             s = ensure_precision(n, 0, st);
@@ -564,7 +582,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             rel = std::sqrt(n->hsc->os.rr) / bn;
             dist = outer_dist(n, o, rel);
         }
-        dist_prev = dist;
+        rel_prev = rel;
     }
     CK(cudaEventRecord(n->ev[2], st));
     CK(cudaEventSynchronize(n->ev[2]));

@@ -87,6 +87,9 @@ inline double geff_err(const net_t *n) {
 inline double outer_dist(const net_t *n, const net_opts &o, double rel) {
     return std::fmax(rel / o.tol_rel, geff_err(n) / eff_tol_geff(o));
 }
+// One line per refinement step on stderr when NETSOLVE_TRACE is set.
+void trace_outer(const net_t *n, const char *who, int outer, int f32, int stop, long long iters,
+                 double rel);
 // Scaled bonds and inner vectors of one precision (allocated on first use).
 net_status ensure_precision(net_t *n, int f32, cudaStream_t st);
 void set_error(const char *fmt, ...);

@@ -87,23 +87,22 @@ def lib(build_if_missing: bool = False):
     L.net_last_error.restype = C.c_char_p
     L.net_labels_noalloc.argtypes = [P(net_desc), P(vp), vp, vp]
     L.net_labels_noalloc.restype = C.c_int
-    if True:
-        L.net_solve_batch.argtypes = [P(vp), C.c_int, P(net_opts), P(net_result)]
-        L.net_solve_batch.restype = C.c_int
-        L.netq_create.argtypes = [C.c_size_t, C.c_int, P(net_opts), P(vp)]
-        L.netq_create.restype = C.c_int
-        L.netq_submit.argtypes = [vp, P(net_desc), P(vp), P(C.c_uint64)]
-        L.netq_submit.restype = C.c_int
-        L.netq_poll.argtypes = [vp, C.c_uint64, P(net_result)]
-        L.netq_poll.restype = C.c_int
-        L.netq_wait.argtypes = [vp, C.c_uint64, C.c_int, P(net_result)]
-        L.netq_wait.restype = C.c_int
-        L.netq_cancel.argtypes = [vp, C.c_uint64]
-        L.netq_cancel.restype = C.c_int
-        L.netq_stats.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_uint64)]
-        L.netq_stats.restype = C.c_int
-        L.netq_destroy.argtypes = [vp]
-        L.netq_destroy.restype = C.c_int
+    L.net_solve_batch.argtypes = [P(vp), C.c_int, P(net_opts), P(net_result)]
+    L.net_solve_batch.restype = C.c_int
+    L.netq_create.argtypes = [C.c_size_t, C.c_int, P(net_opts), P(vp)]
+    L.netq_create.restype = C.c_int
+    L.netq_submit.argtypes = [vp, P(net_desc), P(vp), P(C.c_uint64)]
+    L.netq_submit.restype = C.c_int
+    L.netq_poll.argtypes = [vp, C.c_uint64, P(net_result)]
+    L.netq_poll.restype = C.c_int
+    L.netq_wait.argtypes = [vp, C.c_uint64, C.c_int, P(net_result)]
+    L.netq_wait.restype = C.c_int
+    L.netq_cancel.argtypes = [vp, C.c_uint64]
+    L.netq_cancel.restype = C.c_int
+    L.netq_stats.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_uint64)]
+    L.netq_stats.restype = C.c_int
+    L.netq_destroy.argtypes = [vp]
+    L.netq_destroy.restype = C.c_int
     _lib = L
     return L
 
@@ -207,6 +206,7 @@ class Result:
     inner_launches: int
     status: int
     g_eff_err: float
+    error: str = ""  # message of a non-OK status
 
     @classmethod
     def from_c(cls, r: net_result):
@@ -321,12 +321,19 @@ class Queue:
     def poll(self, ticket):
         r = net_result()
         st = lib().netq_poll(self.h, C.c_uint64(ticket), C.byref(r))
-        return st, (Result.from_c(r) if st != NET_EBUSY else None)
+        return st, (self._result(st, r) if st != NET_EBUSY else None)
 
     def wait(self, ticket, timeout_ms=-1):
         r = net_result()
         st = lib().netq_wait(self.h, C.c_uint64(ticket), int(timeout_ms), C.byref(r))
-        return st, (Result.from_c(r) if st != NET_ETIMEOUT else None)
+        return st, (self._result(st, r) if st != NET_ETIMEOUT else None)
+
+    @staticmethod
+    def _result(st, r):
+        res = Result.from_c(r)
+        if st != NET_OK:
+            res.error = lib().net_last_error().decode(errors="replace")
+        return res
 
     def cancel(self, ticket):
         return lib().netq_cancel(self.h, C.c_uint64(ticket))

@@ -134,13 +134,46 @@ def test_queue_budget_cancel_and_errors(ns):
         ts = [q.submit(d, p) for d, p in specs]
         c = q.cancel(ts[-1])
         assert c in (ns.NET_OK, ns.NET_EBUSY)
-        st, _ = q.wait(tb, timeout_ms=60000)
+        st, r = q.wait(tb, timeout_ms=60000)
         assert st == ns.NET_EINVAL
+        assert "negative" in r.error and f"request {tb}" in r.error
         for t in ts[:-1]:
             st, r = q.wait(t, timeout_ms=60000)
-            assert st == ns.NET_OK
-        st, _ = q.wait(ts[-1], timeout_ms=60000)
+            assert st == ns.NET_OK and r.error == ""
+        st, r = q.wait(ts[-1], timeout_ms=60000)
         assert st == (ns.NET_ECANCELLED if c == ns.NET_OK else ns.NET_OK)
+        if c == ns.NET_OK:
+            assert "cancelled" in r.error
         # a read ticket is gone
         st, _ = q.poll(ts[0])
         assert st == ns.NET_EINVAL
+
+
+def test_queue_reports_not_converged(ns):
+    """A request that cannot meet its tolerance within max_outer refinement
+    steps ends NET_ENOTCONVERGED, and its message reaches the caller."""
+    opts = ns.make_opts(tol_rel=1e-15, tol_geff=1e-15, max_outer=1)
+    dims, planes = netgen.batch_instance(3, smin=64, smax=96)
+    with ns.Queue(mem_budget_bytes=64 << 20, max_slots=2, opts=opts) as q:
+        t = q.submit(dims, planes)
+        st, r = q.wait(t, timeout_ms=60000)
+    assert st == ns.NET_ENOTCONVERGED
+    assert r.outer_iters == 1 and "not converged" in r.error
+
+
+def test_near_critical_3d_converges_alone_and_in_batch(ns):
+    """A 110^3 near-critical percolation network (p = 0.26, lognormal
+    conductances) whose FP64 inner solves plateau for hundreds of iterations:
+    it must converge in a few refinement steps both alone and in a batch."""
+    dims, planes = netgen.request_instance(7)
+    assert dims == (110, 110, 110)
+    a = solo(ns, dims, planes)
+    assert a.status == ns.NET_OK and a.outer_iters <= 20, a
+    others = mixed_nets(5, seed0=300, with3d=False)
+    nets = [ns.Network(dims, planes)] + [ns.Network(d, p) for d, p in others]
+    res = ns.solve_batch(nets)
+    for net in nets:
+        net.close()
+    assert all(r.status == ns.NET_OK for r in res)
+    assert res[0].outer_iters <= 20
+    assert rel(res[0].g_eff, a.g_eff) <= G_TOL
