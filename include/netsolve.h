@@ -68,6 +68,16 @@ typedef enum {
 
 enum { NET_F64 = 0, NET_F32 = 1 };      /* bond conductance dtype */
 enum { NET_MIXED = 0, NET_FP64 = 1 };   /* solver precision */
+/* Refinement scheme (net_opts.refine).  Both keep x and the true residual in
+ * FP64 and run CG on the correction equation in the inner precision.
+ *   NET_REFINE_RELIABLE  after each refinement pass the inner CG continues
+ *                        along its current search direction, with the true
+ *                        residual put in place of the recursive one
+ *                        ("reliable update"); it restarts only after
+ *                        stagnation, a cap or a breakdown.
+ *   NET_REFINE_RESTART   classical iterative refinement: every inner solve
+ *                        starts from a zero correction and p = r. */
+enum { NET_REFINE_RELIABLE = 0, NET_REFINE_RESTART = 1 };
 
 /* Cluster classes returned by net_get_labels. */
 enum {
@@ -99,9 +109,10 @@ typedef struct {
     int precision;           /* NET_MIXED (default) or NET_FP64 */
     double tol_rel;          /* outer stop: ||b - G P||_2 <= tol_rel ||b||_2
                                 (and see tol_geff); default 1e-11 */
-    double tol_inner;        /* inner relative reduction per refinement step
-                                (mixed); default 1e-4 */
-    int max_outer;           /* refinement steps; default 40 */
+    double tol_inner;        /* NET_REFINE_RESTART: deepest relative reduction
+                                asked of one FP32 inner solve; default 1e-4 */
+    int max_outer;           /* refinement passes (true-residual
+                                evaluations); default 200 */
     int64_t max_inner;       /* CG iterations per inner solve; default 200000 */
     int check_every;         /* inner iterations per device-flag check;
                                 0 = choose automatically */
@@ -117,6 +128,14 @@ typedef struct {
                                 residual r is the pressure field scaled to
                                 (p_in, p_out) = (1, 0), so the error of Q_in is
                                 sum_i (P_i - p_out) r_i / (p_in - p_out). */
+    int refine;              /* NET_REFINE_RELIABLE (default) or
+                                NET_REFINE_RESTART */
+    double update_delta;     /* NET_REFINE_RELIABLE with an FP32 inner loop:
+                                a refinement pass is taken once the recursive
+                                residual norm has fallen to update_delta times
+                                its largest value since the last pass (or the
+                                outer targets are reached); default 1e-3,
+                                in (0, 1) */
 } net_opts;
 
 /* Per-solve result and diagnostics. */

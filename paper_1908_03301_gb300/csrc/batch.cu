@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "../../include/netsolve.h"
@@ -21,7 +22,7 @@ namespace {
 __global__ void gather_status_kernel(const InnerScal *const *s, int n, int *stop, long long *iter) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         stop[i] = s[i]->stop;
-        iter[i] = s[i]->iter;
+        iter[i] = s[i]->iter - s[i]->iter0;  // iterations of this pass
     }
 }
 
@@ -173,7 +174,7 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
     for (BatchItem *it : ok) {
         net_t *n = it->net;
         it->rel = n->bnorm > 0.0 ? std::sqrt(n->hsc->os.rr) / n->bnorm : 0.0;
-        it->rel_prev = it->rel;
+        it->prog.start(it->rel, geff_err(n));
         if (n->bnorm == 0.0 || outer_dist(n, it->opts, it->rel) <= 1.0) {
             finish(it, NET_OK);
             continue;
@@ -254,6 +255,20 @@ net_status BatchEngine::rebuild(Group &g, int K) {
 
 net_status BatchEngine::step(int K) {
     if (nrun_ == 0) return NET_OK;
+    const bool tr = trace_on();
+    const auto t0 = std::chrono::steady_clock::now();
+    if (tr) {
+        // running networks and unknowns per group before this step
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) {
+                const Group &g = groups_[d][f];
+                if (g.items.empty()) continue;
+                long long u = 0;
+                for (const BatchItem *it : g.items) u += it->net->n_active;
+                fprintf(stderr, "[trace batch-step %dD %s] running %zu unknowns %lld K %d\n", d + 2,
+                        f ? "f32" : "f64", g.items.size(), u, K);
+            }
+    }
     for (int d = 0; d < 2; d++)
         for (int f = 0; f < 2; f++) {
             Group &g = groups_[d][f];
@@ -291,6 +306,9 @@ net_status BatchEngine::step(int K) {
     CKB(cudaMemcpyAsync(stop.data(), d_stop_, sizeof(int) * n, cudaMemcpyDeviceToHost, st_));
     CKB(cudaMemcpyAsync(iters.data(), d_iter_, sizeof(long long) * n, cudaMemcpyDeviceToHost, st_));
     CKB(cudaStreamSynchronize(st_));
+    if (tr)
+        fprintf(stderr, "[trace batch-step] sweeps %.3f ms\n",
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     // outer passes of every network whose inner solve stopped
     std::vector<BatchItem *> stopped;
     std::vector<int> stop_code, stop_iter;
@@ -316,22 +334,21 @@ net_status BatchEngine::step(int K) {
         BatchItem *it = stopped[j];
         net_t *nt = it->net;
         it->outer++;
-        const double rel_prev = it->rel_prev;
         it->rel = std::sqrt(nt->hsc->os.rr) / nt->bnorm;
         const double dist = outer_dist(nt, it->opts, it->rel);
-        it->rel_prev = it->rel;
+        const bool stalled = it->prog.stalled(it->rel, geff_err(nt), stall_limit(it->opts));
         trace_outer(nt, "batch", it->outer, it->f32, stop_code[j], stop_iter[j], it->rel);
         if (dist <= 1.0) {
             finish(it, NET_OK);
         } else if (it->outer >= it->opts.max_outer) {
             set_error("batch: not converged after %d refinement steps", it->outer);
             finish(it, NET_ENOTCONVERGED);
-        } else if (it->f32 && it->rel > 0.5 * rel_prev) {
+        } else if (it->f32 && stalled) {
             to_fp64.push_back(it);
         }
     }
     for (BatchItem *it : to_fp64) {
-        // an FP32 refinement step that did not halve the residual: continue in FP64
+        // FP32 passes that stopped making progress: continue in FP64
         net_t *nt = it->net;
         set_stop_kernel<<<1, 1, 0, st_>>>(&nt->dsc->in[0], 1);
         net_status s = ensure_precision(nt, 0, st_);
@@ -344,6 +361,7 @@ net_status BatchEngine::step(int K) {
         it->fallback = 1;
         s = outer_pass(it, 0, 0);
         if (s != NET_OK) return s;
+        it->prog.start(it->rel, geff_err(nt));
         Group &g64 = group_of(nt->g.ndim, 0);
         g64.items.push_back(it);
         g64.dirty = true;
@@ -394,8 +412,8 @@ NET_API net_status net_solve_batch(net_t *const *nets, int count, const net_opts
     net_opts o;
     net_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.tol_rel > 0.0) || !(o.tol_inner > 0.0) || o.max_outer < 1 || o.max_inner < 1) {
-        set_error("net_solve_batch: bad tolerances or caps");
+    if (!opts_valid(o)) {
+        set_error("net_solve_batch: %s", std::string(last_error()).c_str());
         return NET_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)o.stream;

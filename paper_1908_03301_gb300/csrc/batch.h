@@ -25,7 +25,7 @@ struct BatchItem {
     int outer = 0;
     long long inner_total = 0;
     double rel = 0.0;
-    double rel_prev = 0.0;   // relative residual before the last refinement step
+    Progress prog;           // FP32 progress watch (switch to FP64)
     int fallback = 0;
     bool done = false;
     net_result res{};

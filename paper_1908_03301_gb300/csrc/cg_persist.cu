@@ -443,7 +443,37 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
     }
 }
 
+// A launch that continues the recursion (iter > 0 after a refinement pass)
+// starts with a non-first sweep, which reads its neighbours' edge rows of r,
+// q, p from the halo copies of parity 1.  The refinement pass replaced r, so
+// those copies are rewritten from the vectors here (one CTA per persistent
+// CTA, same row partition).
+__global__ void persist_resume_kernel(PersistArgs a) {
+    if (a.s->iter == 0) return;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int px = a.g.px, ny = a.g.ny;
+    const int row0 = (int)((long long)c * ny / G), row1 = (int)((long long)(c + 1) * ny / G);
+    const long long base = a.g.pad;
+    const float *src[3];
+    src[H_R] = a.r;
+    src[H_Q] = a.q;
+    src[H_P] = a.p;
+    for (int e = 0; e < 2; e++) {
+        const long long row = e == 0 ? row0 : row1 - 1;
+        for (int arr = 0; arr < 3; arr++) {
+            const float *from = src[arr] + base + row * px;
+            float *to = hb_row(a, 1, c, e, arr, G, px);
+            for (int i = threadIdx.x; i < px; i += blockDim.x) to[i] = from[i];
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_persist_resume(const PersistArgs &a, int grid, cudaStream_t st) {
+    persist_resume_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 bool persist_applies(const Geom &g, int f32) {
     return f32 && g.ndim == 2 && g.px <= WMAX && g.ny >= 2;

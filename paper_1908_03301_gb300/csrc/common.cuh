@@ -50,19 +50,25 @@ enum : uint8_t {
 // the next values, after every other CTA has read them.
 struct InnerScal {
     double alpha, beta;   // step lengths for the next iteration
-    double rho0;          // ||r_0||^2 of this inner solve
-    double tol2;          // stop when ||r||^2 <= tol2 * rho0
+    double rho0;          // ||r||^2 when this pass was armed
+    double tol2;          // pass target: ||r||^2 <= tol2 * rho0
     double rho;           // last directly computed ||r||^2
     double best;          // smallest ||r||^2 seen (stagnation watch)
+    double maxrr;         // largest ||r||^2 since the pass was armed
+    double delta2;        // reliable update due at ||r||^2 <= delta2 * maxrr (0: off)
     long long best_iter;
-    long long iter;       // iteration kernels that did work in this solve
+    long long iter;       // iterations since the CG recursion (re)started
+    long long iter0;      // iter when this pass was armed
     long long max_iter;
     long long stag_window;
     int stop;             // 0 run, 1 converged, 2 cap, 3 stagnated, 4 breakdown,
-                          // 5 device wait timed out
+                          // 5 device wait timed out, 6 refinement pass due
+                          // (alpha, beta of the next iteration still pending)
     int err;              // set by a CTA whose bounded wait gave up
     unsigned int counter; // CTA arrival counter of the running launch
+    int reliable;         // passes continue the recursion (stop 6) instead of restarting
 };
+static_assert(sizeof(InnerScal) % 8 == 0, "InnerScal is copied as 64-bit words");
 
 // Sums of one outer (FP64) residual pass.
 struct OuterScal {
@@ -159,6 +165,13 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], const int (&ops)[NV
 // four reduced sums v = {<p,q>, <r,q>, <q,q>, <r,r>} of iteration k:
 // alpha_k = <r,r>/<p,q>, beta_k = ||r - alpha q||^2 / <r,r> with the square
 // expanded; convergence, cap, stagnation and breakdown tests.
+//
+// Restart mode ends the pass when ||r_k|| reaches the pass target (stop 1,
+// y consistent with r_k).  Reliable mode first takes alpha_k, beta_k and
+// ends the pass when the next residual ||r_k - alpha_k q_k|| reaches the
+// target or has fallen to delta times its largest value since the pass was
+// armed (stop 6): the refinement pass then folds y + alpha_k p_k into x,
+// recomputes r in FP64 and the recursion continues from p_k.
 __device__ __forceinline__ void finish_iteration(InnerScal *s, long long k, const double (&v)[4]) {
     const double pq = v[0], rq = v[1], qq = v[2], rr = v[3];
     s->rho = rr;
@@ -167,7 +180,7 @@ __device__ __forceinline__ void finish_iteration(InnerScal *s, long long k, cons
         s->stop = 5;
         return;
     }
-    if (rr <= s->tol2 * s->rho0 || rr == 0.0) {
+    if (rr == 0.0 || (!s->reliable && rr <= s->tol2 * s->rho0)) {
         s->stop = 1;
         return;
     }
@@ -180,6 +193,13 @@ __device__ __forceinline__ void finish_iteration(InnerScal *s, long long k, cons
     if (!(rn1 > 0.0)) rn1 = 0.0;  // cancellation: restart along the residual
     s->alpha = a;
     s->beta = rn1 / rr;
+    if (s->reliable) {
+        s->maxrr = fmax(s->maxrr, rr);
+        if (rn1 <= s->tol2 * s->rho0 || rn1 <= s->delta2 * s->maxrr) {
+            s->stop = 6;
+            return;
+        }
+    }
     if (rr < 0.25 * s->best) {
         s->best = rr;
         s->best_iter = k;

@@ -80,13 +80,19 @@ struct OuterArgs {
     const double *dis;
     double *x;
     const void *y;        // inner correction (T), read when apply_corr
-    void *r_out;          // scaled residual for the next inner solve (T):
-                          // buffer r[0] of the inner vectors
+    void *r_buf[2];       // inner residual buffers (T) of the armed precision;
+                          // r_buf[1] == r_buf[0] for in-place inner kernels
+    const void *p_buf[2]; // search directions (T) of the correction's precision
     int inner_f32;
     int apply_corr;       // first apply x += D^-1/2 y (separate kernel)
     int corr_f32;         // dtype of y
     OuterScal *os;
     InnerScal *is;        // inner scalars to arm for the next inner solve
+    const InnerScal *is_corr;  // scalars of the pass that produced y (apply_corr)
+    int reliable;         // arm the next pass in reliable mode
+    int allow_cont;       // continue the recursion if the last pass ended with
+                          // stop 6 (same precision, correction applied)
+    double delta2;        // reliable-update threshold (squared) for the next pass
     double tol_floor;     // smallest relative reduction asked of the inner solve
     double tol_rel;       // outer tolerance (relative 2-norm residual)
     double tol_geff;      // outer tolerance on the estimated relative error of G_eff
@@ -96,5 +102,9 @@ struct OuterArgs {
 };
 int outer_grid_blocks(const Geom &g);
 cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st);
+// Before a persistent-kernel launch that continues a recursion (iter > 0):
+// refresh the halo copies of r, q, p that the first sweep reads (r was
+// replaced by the refinement pass).  Does nothing when iter == 0.
+cudaError_t launch_persist_resume(const PersistArgs &a, int grid, cudaStream_t st);
 
 }  // namespace netsolve

@@ -251,12 +251,23 @@ struct OTile {
 template <typename TI>
 __global__ void __launch_bounds__(NT)
 correct_kernel(Geom g, const double *__restrict__ dis, double *__restrict__ x,
-               const TI *__restrict__ yc) {
+               TI *__restrict__ yc, const TI *p0, const TI *p1, const InnerScal *is) {
+    // A pass that ended with stop 6 still owes the step alpha_k p_k of the
+    // recursion (Sec. IV refinement with the recursion kept): fold it in with
+    // y and clear y, which the continuing recursion accumulates from zero.
+    const bool owe = is->stop == 6;
+    const double a = is->alpha;
+    const TI *__restrict__ p = (is->iter & 1) ? p1 : p0;
     const long long n = (long long)g.px * g.ny * g.nz;
     for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
          t += (long long)gridDim.x * NT) {
         const long long i = g.pad + t;
-        x[i] = fma(dis[i], (double)yc[i], x[i]);
+        double d = (double)yc[i];
+        if (owe) {
+            d = fma(a, (double)p[i], d);
+            yc[i] = TI(0);
+        }
+        x[i] = fma(dis[i], d, x[i]);
     }
 }
 
@@ -264,14 +275,23 @@ template <typename GT, typename TI, int NDIM>
 __global__ void __launch_bounds__(NT)
 outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
              const GT *__restrict__ g2, const double *__restrict__ dis, const double *__restrict__ x,
-             TI *__restrict__ r_out, OuterScal *os,
-             InnerScal *is, double tol_floor, double tol_rel, double tol_geff, double bnorm,
-             long long max_inner, long long stag_window, double *partials) {
+             TI *r_out0, TI *r_out1, OuterScal *os,
+             InnerScal *is, int reliable, int allow_cont, double delta2, double tol_floor, double tol_rel,
+             double tol_geff, double bnorm, long long max_inner, long long stag_window,
+             double *partials) {
     using OT = OTile<NDIM>;
     constexpr int TW = OT::TW, TH = OT::TH, TD = OT::TD;
     __shared__ double sx[OT::ZP * OT::SH * OT::SW];
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, z0 = blockIdx.z * TD;
     const GT *gp[3] = {g0, g1, g2};
+    // Continue the recursion when the last pass asked for this refinement
+    // (stop 6): the new residual goes where the next iteration reads r
+    // (buffer iter & 1).  Otherwise restart: buffer 0, iteration 0.  The
+    // scalars are read here, before the last CTA re-arms them.
+    const bool cont = allow_cont && is->stop == 6;
+    const long long it_prev = is->iter;
+    const double rho_prev = is->rho;
+    TI *__restrict__ r_out = (cont && (it_prev & 1)) ? r_out1 : r_out0;
 
     // stage x over the tile and its halo (x is read-only in this kernel; the
     // correction was applied by correct_kernel before it)
@@ -348,10 +368,25 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     if (gerr > 0.0) t = fmin(t, 0.5 * tol_geff / gerr);
     t = fmin(0.5, fmax(t, tol_floor));
     is->tol2 = t * t;
+    is->maxrr = v[2];
+    is->delta2 = reliable ? delta2 : 0.0;
+    is->reliable = reliable;
+    if (cont) {
+        // r_k is replaced by the true residual r^ and the step alpha_k was
+        // folded into x, so the next iteration takes alpha = 0 and
+        // p = r^ + beta p_k with beta = ||r^||^2 / ||r_k||^2.  A true residual
+        // above the last recursive one means the recursion has drifted: its
+        // direction is dropped (beta = 0), which restarts CG in place.
+        is->beta = v[2] < rho_prev ? v[2] / rho_prev : 0.0;
+        is->iter = it_prev;
+    } else {
+        is->beta = 0.0;
+        is->iter = 0;
+    }
+    is->iter0 = is->iter;
     is->best = v[2];
-    is->best_iter = 0;
-    is->iter = 0;
-    is->max_iter = max_inner;
+    is->best_iter = is->iter;
+    is->max_iter = is->iter + max_inner;
     is->stag_window = stag_window;
     is->err = 0;
     is->counter = 0u;
@@ -396,8 +431,8 @@ template <typename GT, typename TI, int NDIM>
 cudaError_t launch_outer_t(const OuterArgs &a, cudaStream_t st) {
     outer_kernel<GT, TI, NDIM><<<outer_grid<NDIM>(a.g), NT, 0, st>>>(
         a.g, (const GT *)a.graw[0], (const GT *)a.graw[1], (const GT *)a.graw[2], a.dis, a.x,
-        (TI *)a.r_out, a.os, a.is, a.tol_floor, a.tol_rel, a.tol_geff, a.bnorm, a.max_inner,
-        a.stag_window, a.partials);
+        (TI *)a.r_buf[0], (TI *)a.r_buf[1], a.os, a.is, a.reliable, a.allow_cont, a.delta2, a.tol_floor,
+        a.tol_rel, a.tol_geff, a.bnorm, a.max_inner, a.stag_window, a.partials);
     return cudaGetLastError();
 }
 
@@ -427,9 +462,13 @@ cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st) {
         long long nb = ((long long)a.g.px * a.g.ny * a.g.nz + NT - 1) / NT;
         if (nb > 152LL * 16) nb = 152LL * 16;
         if (a.corr_f32)
-            correct_kernel<float><<<(int)nb, NT, 0, st>>>(a.g, a.dis, a.x, (const float *)a.y);
+            correct_kernel<float><<<(int)nb, NT, 0, st>>>(a.g, a.dis, a.x, (float *)a.y,
+                                                          (const float *)a.p_buf[0],
+                                                          (const float *)a.p_buf[1], a.is_corr);
         else
-            correct_kernel<double><<<(int)nb, NT, 0, st>>>(a.g, a.dis, a.x, (const double *)a.y);
+            correct_kernel<double><<<(int)nb, NT, 0, st>>>(a.g, a.dis, a.x, (double *)a.y,
+                                                           (const double *)a.p_buf[0],
+                                                           (const double *)a.p_buf[1], a.is_corr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

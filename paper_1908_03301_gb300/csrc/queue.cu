@@ -187,9 +187,9 @@ NET_API net_status netq_create(size_t mem_budget_bytes, int max_slots, const net
     if (opts) q->opts = *opts;
     q->opts.x0 = nullptr;
     q->opts.stream = nullptr;
-    if (!(q->opts.tol_rel > 0.0) || !(q->opts.tol_inner > 0.0) || q->opts.max_outer < 1 || q->opts.max_inner < 1) {
+    if (!opts_valid(q->opts)) {
         delete q;
-        set_error("netq_create: bad tolerances or caps");
+        set_error("netq_create: %s", std::string(last_error()).c_str());
         return NET_EINVAL;
     }
     if (cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking) != cudaSuccess) {

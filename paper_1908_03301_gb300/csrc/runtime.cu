@@ -42,10 +42,31 @@ void set_error(const char *fmt, ...) {
 
 const char *last_error() { return g_err.c_str(); }
 
+bool opts_valid(const net_opts &o) {
+    if (o.precision != NET_MIXED && o.precision != NET_FP64) {
+        set_error("bad precision");
+        return false;
+    }
+    if (!(o.tol_rel > 0.0) || !(o.tol_inner > 0.0) || o.max_outer < 1 || o.max_inner < 1) {
+        set_error("bad tolerances or caps");
+        return false;
+    }
+    if (o.refine != NET_REFINE_RELIABLE && o.refine != NET_REFINE_RESTART) {
+        set_error("bad refine mode");
+        return false;
+    }
+    if (!(o.update_delta >= 0.0 && o.update_delta < 1.0)) {  // 0 = default
+        set_error("update_delta must be in (0, 1)");
+        return false;
+    }
+    return true;
+}
+
+bool trace_on() { return getenv("NETSOLVE_TRACE") != nullptr; }
+
 void trace_outer(const net_t *n, const char *who, int outer, int f32, int stop, long long iters,
                  double rel) {
-    static const bool on = getenv("NETSOLVE_TRACE") != nullptr;
-    if (!on) return;
+    if (!trace_on()) return;
     fprintf(stderr, "[trace %s %p %lldx%lldx%lld] step %d %s stop %d iters %lld rel %.3e gerr %.3e\n", who,
             (const void *)n, (long long)n->g.nx, (long long)n->g.ny, (long long)n->g.nz, outer,
             f32 ? "f32" : "f64", stop, iters, rel, geff_err(n));
@@ -273,7 +294,7 @@ InnerArgs inner_args(net_t *n, int f32) {
     return a;
 }
 
-OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op) {
+OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op, int inplace) {
     const int k = f32 ? 0 : 1, kc = corr_f32 ? 0 : 1;
     OuterArgs o{};
     o.g = n->g;
@@ -285,23 +306,37 @@ OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_
     o.y = n->vec[kc];
     o.apply_corr = apply_corr && n->vec[kc] != nullptr;
     o.corr_f32 = corr_f32;
-    const size_t es = f32 ? 4 : 8;
-    o.r_out = (char *)n->vec[k] + 1 * (size_t)n->g.len * es;
+    // inner vectors: y, r0, r1, p0, p1, q0, q1 (in-place kernels use r0, p0, q0)
+    const size_t L = (size_t)n->g.len, es = f32 ? 4 : 8, esc = corr_f32 ? 4 : 8;
+    char *v = (char *)n->vec[k];
+    o.r_buf[0] = v + 1 * L * es;
+    o.r_buf[1] = inplace ? o.r_buf[0] : v + 2 * L * es;
+    const char *vc = (const char *)n->vec[kc];
+    o.p_buf[0] = vc ? vc + 3 * L * esc : nullptr;
+    o.p_buf[1] = vc ? (inplace ? o.p_buf[0] : vc + 4 * L * esc) : nullptr;
     o.inner_f32 = f32;
     o.os = &n->dsc->os;
     o.is = &n->dsc->in[k];
-    o.tol_floor = f32 ? op.tol_inner : 0.0;
+    o.is_corr = &n->dsc->in[kc];
+    const bool rel_mode = op.refine != NET_REFINE_RESTART;
+    o.reliable = rel_mode;
+    o.allow_cont = rel_mode && o.apply_corr && k == kc;
+    const double dl = op.update_delta > 0.0 && op.update_delta < 1.0 ? op.update_delta : 1e-3;
+    o.delta2 = rel_mode && f32 ? dl * dl : 0.0;
+    o.tol_floor = f32 && !rel_mode ? op.tol_inner : 0.0;
     o.tol_rel = op.tol_rel;
     o.tol_geff = op.tol_geff > 0.0 ? op.tol_geff : 1e-9;
     o.bnorm = n->bnorm;
     o.max_inner = op.max_inner;
-    // An FP32 inner loop that has not halved its residual norm for this many
-    // iterations restarts from a fresh FP64 residual.  FP64 CG has no
-    // precision floor at these targets, and on near-critical networks its
-    // residual plateaus for hundreds of iterations between drops; a restart
-    // there throws away the Krylov space, so its window is much longer.
+    // An inner loop that has not halved its residual norm for this many
+    // iterations ends its pass, and the next pass restarts CG.  On
+    // near-critical networks the residual plateaus for hundreds of iterations
+    // between drops, and a restart throws away the Krylov space, so the window
+    // is long unless FP32 passes restart anyway (restart mode), where a stall
+    // is more likely the FP32 precision floor.  (In reliable mode that floor
+    // shows at the pass boundaries, in the true residual.)
     const long long side = std::max(n->g.nx, std::max(n->g.ny, n->g.nz));
-    o.stag_window = f32 ? std::max(400LL, 8LL * side) : std::max(4000LL, 64LL * side);
+    o.stag_window = f32 && !rel_mode ? std::max(400LL, 8LL * side) : std::max(4000LL, 64LL * side);
     o.partials = n->partials;
     return o;
 }
@@ -428,11 +463,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     net_opts_default(&o);
     if (o_in) o = *o_in;
     memset(r, 0, sizeof(*r));
-    if (o.precision != NET_MIXED && o.precision != NET_FP64) { set_error("bad precision"); return r->status = NET_EINVAL; }
-    if (!(o.tol_rel > 0.0) || !(o.tol_inner > 0.0) || o.max_outer < 1 || o.max_inner < 1) {
-        set_error("bad tolerances or caps");
-        return r->status = NET_EINVAL;
-    }
+    if (!opts_valid(o)) return r->status = NET_EINVAL;
     cudaStream_t st = o.stream ? (cudaStream_t)o.stream : n->stream;
     const Geom &G = n->g;
     const double dP = G.p_in - G.p_out;
@@ -469,7 +500,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         }
     }
     // first residual pass (no correction pending)
-    OuterArgs oa = outer_args(n, f32, 0, f32, o);
+    OuterArgs oa = outer_args(n, f32, 0, f32, o, use_persist_kernel(n, f32));
     CK(launch_outer(oa, st));
     CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -481,7 +512,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     float inner_ms = 0.f;
     int fallback = 0;
     net_status status = NET_OK;
-    double rel_prev = rel;
+    Progress prog;
+    prog.start(rel, geff_err(n));
     while (true) {
         if (dist <= 1.0 || bn == 0.0) break;
         if (outer >= o.max_outer) { status = NET_ENOTCONVERGED; break; }
@@ -510,6 +542,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             pa.bar_count = n->ps_bar;
             pa.bar_gen = n->ps_bar + 1;
             pa.err = n->ps_err;
+            CK(launch_persist_resume(pa, n->ps_grid, st));
             CK(launch_persist(pa, n->ps_grid, st));
             chunks = 0;
             launches += 1;
@@ -547,25 +580,22 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         CK(cudaStreamSynchronize(st));
         inner_ms += ms;
         launches += chunks * n->gk[k];
-        inner_total += hs->iter;
+        inner_total += hs->iter - hs->iter0;
         if (hs->stop == 5) {
             set_error("a bounded device wait in the CG kernel gave up");
             return r->status = NET_ETIMEOUT;
         }
         outer++;
         // apply the correction, new residual; arm the same precision again
-        int next_f32 = f32;
-        oa = outer_args(n, next_f32, 1, f32, o);
+        oa = outer_args(n, f32, 1, f32, o, use_persist_kernel(n, f32));
         CK(launch_outer(oa, st));
         CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rel = std::sqrt(n->hsc->os.rr) / bn;
         dist = outer_dist(n, o, rel);
-        trace_outer(n, "solve", outer, f32, hs->stop, hs->iter, rel);
-        // An FP32 refinement step that did not halve the residual has met
-        // the FP32 limit: continue in FP64.  (The G_eff error estimate is
-        // not monotone under CG and is not used for this decision.)
-        if (f32 && dist > 1.0 && rel > 0.5 * rel_prev) {
+        trace_outer(n, "solve", outer, f32, hs->stop, hs->iter - hs->iter0, rel);
+        // FP32 passes that stopped making progress: continue in FP64
+        if (prog.stalled(rel, geff_err(n), stall_limit(o)) && f32 && dist > 1.0) {
             f32 = 0;
             fallback = 1;
             s = ensure_precision(n, 0, st);
@@ -575,14 +605,14 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
                 if (s != NET_OK) return r->status = s;
             }
             // re-arm the FP64 inner solve from the current x (no correction pending)
-            oa = outer_args(n, 0, 0, 0, o);
+            oa = outer_args(n, 0, 0, 0, o, use_persist_kernel(n, 0));
             CK(launch_outer(oa, st));
             CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             rel = std::sqrt(n->hsc->os.rr) / bn;
             dist = outer_dist(n, o, rel);
+            prog.start(rel, geff_err(n));
         }
-        rel_prev = rel;
     }
     CK(cudaEventRecord(n->ev[2], st));
     CK(cudaEventSynchronize(n->ev[2]));
@@ -628,10 +658,12 @@ NET_API void net_opts_default(net_opts *o) {
     o->precision = NET_MIXED;
     o->tol_rel = 1e-11;
     o->tol_inner = 1e-4;
-    o->max_outer = 40;
+    o->max_outer = 200;
     o->max_inner = 200000;
     o->check_every = 0;
     o->tol_geff = 1e-9;
+    o->refine = NET_REFINE_RELIABLE;
+    o->update_delta = 1e-3;
 }
 
 NET_API net_status net_create(const net_desc *desc, const void *const g[3], net_t **out) {

@@ -87,7 +87,33 @@ inline double geff_err(const net_t *n) {
 inline double outer_dist(const net_t *n, const net_opts &o, double rel) {
     return std::fmax(rel / o.tol_rel, geff_err(n) / eff_tol_geff(o));
 }
+// Progress of the FP32 refinement passes.  A pass that halves neither the
+// best relative residual nor the best G_eff error estimate so far is a stall;
+// FP32 has reached its limit after `limit` stalls in a row (3 when the CG
+// recursion is kept across passes, whose residual may rise between them; 1
+// for restarted passes).  Then the inner loop continues in FP64.
+struct Progress {
+    double best_rel = 0.0, best_gerr = 0.0;
+    int stall = 0;
+    void start(double rel, double gerr) {
+        best_rel = rel;
+        best_gerr = gerr;
+        stall = 0;
+    }
+    bool stalled(double rel, double gerr, int limit) {
+        const bool gain = rel < 0.5 * best_rel || gerr < 0.5 * best_gerr;
+        best_rel = std::fmin(best_rel, rel);
+        best_gerr = std::fmin(best_gerr, gerr);
+        stall = gain ? 0 : stall + 1;
+        return stall >= limit;
+    }
+};
+inline int stall_limit(const net_opts &o) { return o.refine == NET_REFINE_RESTART ? 1 : 3; }
+// Options check shared by every solve entry point.
+bool opts_valid(const net_opts &o);
+
 // One line per refinement step on stderr when NETSOLVE_TRACE is set.
+bool trace_on();
 void trace_outer(const net_t *n, const char *who, int outer, int f32, int stop, long long iters,
                  double rel);
 // Scaled bonds and inner vectors of one precision (allocated on first use).
@@ -99,7 +125,8 @@ net_status make_geom(const net_desc *d, Geom *g);
 long long plane_elems(const Geom &g, int d);
 size_t net_footprint_bytes(const Geom &g, int raw_f32);
 InnerArgs inner_args(net_t *n, int f32);
-OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op);
+OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op,
+                     int inplace = 0);
 net_status setup_network(net_t *n, const void *const g[3], int on_device);
 void release_network(net_t *n);
 net_status create_network(const net_desc *desc, const void *const g[3], net_t **out);

@@ -19,6 +19,7 @@ NET_OK, NET_EINVAL, NET_ENOMEM, NET_EBUDGET, NET_ENOTCONVERGED, NET_ETIMEOUT, NE
     NET_ECANCELLED, NET_EBUSY = range(9)
 NET_F64, NET_F32 = 0, 1
 NET_MIXED, NET_FP64 = 0, 1
+NET_REFINE_RELIABLE, NET_REFINE_RESTART = 0, 1
 STATUS_NAMES = ["NET_OK", "NET_EINVAL", "NET_ENOMEM", "NET_EBUDGET", "NET_ENOTCONVERGED",
                 "NET_ETIMEOUT", "NET_ECUDA", "NET_ECANCELLED", "NET_EBUSY"]
 
@@ -33,7 +34,7 @@ class net_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol_rel", C.c_double), ("tol_inner", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int64), ("check_every", C.c_int),
                 ("x0", C.c_void_p), ("x0_on_device", C.c_int), ("stream", C.c_void_p),
-                ("tol_geff", C.c_double)]
+                ("tol_geff", C.c_double), ("refine", C.c_int), ("update_delta", C.c_double)]
 
 
 class net_result(C.Structure):
@@ -126,8 +127,13 @@ def opts_default() -> net_opts:
 
 
 def make_opts(precision=NET_MIXED, tol_rel=None, tol_inner=None, max_outer=None,
-              max_inner=None, check_every=None, stream=None, tol_geff=None) -> net_opts:
+              max_inner=None, check_every=None, stream=None, tol_geff=None, refine=None,
+              update_delta=None) -> net_opts:
     o = opts_default()
+    if refine is not None:
+        o.refine = refine
+    if update_delta is not None:
+        o.update_delta = update_delta
     if tol_geff is not None:
         o.tol_geff = tol_geff
     o.precision = precision

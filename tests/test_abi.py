@@ -62,3 +62,35 @@ def test_host_side_validation_without_gpu(so):
     assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
     assert L.net_solve(None, None, None) == ns.NET_EINVAL
     assert L.net_destroy(None) == ns.NET_OK
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of net_desc, net_opts and net_result have the
+    header's field offsets and sizes (compiled with the host C compiler)."""
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    structs = {"net_desc": ns.net_desc, "net_opts": ns.net_opts, "net_result": ns.net_result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "netsolve.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        cname, field, val = line.split()
+        py = structs[cname]
+        expect = ctypes.sizeof(py) if field == "sizeof" else getattr(py, field).offset
+        assert int(val) == expect, (cname, field, int(val), expect)
+        seen += 1
+    assert seen == sum(len(p._fields_) + 1 for p in structs.values())

@@ -229,3 +229,67 @@ def test_geff_error_estimate_tracks_actual_error(ns, tol_rel):
     actual = rel(r.g_eff, ref.g_eff)
     assert actual > 1e-13  # the early stop left a measurable error
     assert 0.8 <= r.g_eff_err / actual <= 1.25, (r.g_eff_err, actual)
+
+
+# ------------------------------------------------- refinement modes, kernels
+@pytest.fixture
+def kernel_env():
+    import os
+
+    old = os.environ.get("NETSOLVE_KERNEL")
+    yield os.environ
+    if old is None:
+        os.environ.pop("NETSOLVE_KERNEL", None)
+    else:
+        os.environ["NETSOLVE_KERNEL"] = old
+
+
+def _ill_conditioned(dims, seed):
+    gen = netgen.rng(seed)
+    return netgen.percolate(netgen.lognormal_iid(dims, gen, 1.5), 0.62, gen)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("kernel,dims", [("persist", (150, 131)), ("sweep", (150, 131)),
+                                         ("tiled", (150, 131)), ("sweep", (23, 30, 27)),
+                                         ("tiled", (23, 30, 27))])
+def test_refine_modes_every_kernel(ns, kernel_env, kernel, dims, refine):
+    """Reliable updates (the recursion kept across refinement passes, with
+    the true residual put in place of the recursive one) and classical
+    restarted refinement reach the oracle's G_eff and pressures through each
+    inner-loop kernel: the persistent in-place kernel, the double-buffered
+    sweep kernel and the tiled kernel."""
+    kernel_env["NETSOLVE_KERNEL"] = kernel
+    planes = _ill_conditioned(dims, 40 + len(dims))
+    ref = oracle.solve(dims, planes, tol=1e-13)
+    with ns.Network(dims, planes) as net:
+        r = net.solve(ns.make_opts(refine=refine))
+        P = net.pressure()
+    assert r.status == ns.NET_OK, r
+    assert rel(r.g_eff, ref.g_eff) <= G_TOL, (r.g_eff, ref.g_eff)
+    assert np.max(np.abs(P - ref.P)) <= P_TOL
+    if refine == ns.NET_REFINE_RELIABLE:
+        assert r.outer_iters >= 2  # the recursion was carried across passes
+
+
+def test_reliable_updates_save_iterations(ns):
+    """On an ill-conditioned network the FP32 inner loop with reliable
+    updates needs no more CG iterations than restarted refinement."""
+    dims = (256, 256)
+    planes = _ill_conditioned(dims, 77)
+    with ns.Network(dims, planes) as net:
+        a = net.solve(ns.make_opts(refine=ns.NET_REFINE_RELIABLE))
+        b = net.solve(ns.make_opts(refine=ns.NET_REFINE_RESTART))
+    assert a.status == ns.NET_OK and b.status == ns.NET_OK
+    assert rel(a.g_eff, b.g_eff) <= G_TOL
+    assert a.inner_iters <= 1.1 * b.inner_iters, (a.inner_iters, b.inner_iters)
+
+
+def test_refine_options_are_checked(ns):
+    dims = (20, 20)
+    with ns.Network(dims, netgen.uniform(dims)) as net:
+        for kw in ({"refine": 7}, {"update_delta": 1.5}, {"update_delta": -0.1}):
+            r = net.solve(ns.make_opts(**kw), check=False)
+            assert r.status == ns.NET_EINVAL, kw
+        r = net.solve(ns.make_opts(update_delta=0.01))
+        assert r.status == ns.NET_OK and rel(r.g_eff, 20 / 19) <= 1e-12
