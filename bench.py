@@ -434,19 +434,24 @@ def run_perc3d(a):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(a):
+def run_batch(a, rank=0, world=1, local=0):
     """512 independent 2D networks (sides 64..1024, lognormal sigma=1, even
-    ones percolated at p=0.55) created and solved together per step."""
+    ones percolated at p=0.55) created and solved together per step.  Under
+    torchrun the networks are shared out over the ranks (longest first by
+    estimated work, no data-path collective); the step time is the max over
+    ranks, so the value is strong-scaling throughput of the fixed set."""
     import torch
 
-    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netgen, replicas
     from paper_1908_03301_gb300 import netsolve as ns
 
-    ns.lib(build_if_missing=True)
-    specs = [netgen.batch_instance(i) for i in range(a.batch_count)]
-    dev = torch.device("cuda", 0)
+    ns.lib(build_if_missing=(world == 1))
+    all_dims = [netgen.batch_instance_dims(i) for i in range(a.batch_count)]
+    mine = replicas.my_share(all_dims, rank, world)
+    specs = [netgen.batch_instance(i) for i in mine]
+    dev = torch.device("cuda", local)
     tpl = [[torch.from_numpy(g).to(dev) for g in planes] for _, planes in specs]
-    nodes = sum(d[0] * d[1] for d, _ in specs)
+    nodes = sum(d[0] * d[1] for d in all_dims)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def one():
@@ -456,31 +461,45 @@ def run_batch(a):
             n.close()
         return res
 
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
     for _ in range(a.warmup):
         one()
+    torch.cuda.synchronize()
+    barrier()
     times, res = [], None
-    with Clocks(0) as clk:
+    with Clocks(local) as clk:
         for _ in range(a.steps):
             flush.zero_()
             torch.cuda.synchronize()
+            barrier()
             t = time.perf_counter()
             res = one()
             torch.cuda.synchronize()
-            times.append(time.perf_counter() - t)
+            times.append(replicas.max_over_ranks(time.perf_counter() - t, device=dev))
     clocks = clk.summary()
-    ui = sum(r.inner_iters * r.n_active for r in res)
-    ok = sum(r.status == 0 for r in res)
-    lat = sorted(r.ms for r in res)
+    local_res = {i: (r.status, r.inner_iters * r.n_active, r.ms, r.fp64_fallback)
+                 for i, r in zip(mine, res)}
+    allr = replicas.gather_results(local_res, a.batch_count)
+    if rank != 0:
+        return
+    ui = sum(x[1] for x in allr)
+    ok = sum(x[0] == 0 for x in allr)
+    lat = sorted(x[2] for x in allr)
     line = {"metric": METRIC, "workload": "batch", "value": a.batch_count * len(times) / sum(times),
-            "unit": "solves/s", "ms_per_step": statistics.mean(times) * 1e3, "steps": len(times),
-            "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "unit": "solves/s", "n_gpus": world, "ms_per_step": statistics.mean(times) * 1e3,
+            "steps": len(times), "warmup": a.warmup, "scaling": "strong", "dtype": "f32+f64",
+            "data": "synthetic",
             "config": {"workload": f"{a.batch_count} 2D networks, sides U{{64..1024}}, lognormal "
                                    "sigma=1, even ones percolated p=0.55; created + net_solve_batch",
-                       "nodes": nodes, "tol_rel": TOL_REL},
+                       "nodes": nodes, "tol_rel": TOL_REL,
+                       "parallelism": f"networks sharded over {world} GPU(s), no collective"},
             "converged": ok, "unknown_iterations_per_s": ui / statistics.mean(times),
             "algorithmic_gbs": 40 * ui / statistics.mean(times) / 1e9,
             "per_network_ms_p50": lat[len(lat) // 2], "per_network_ms_p99": lat[int(0.99 * (len(lat) - 1))],
-            "fp64_fallbacks": sum(r.fp64_fallback for r in res), "clocks": clocks}
+            "fp64_fallbacks": sum(x[3] for x in allr), "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -540,12 +559,13 @@ def main():
     if a.profile_solve:
         run_profile_solve(a)
         return
-    if a.workload != "fbm2048" and a.impl == "ours":
-        {"perc3d": run_perc3d, "batch": run_batch, "serve": run_serve}[a.workload](a)
-        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.workload in ("perc3d", "serve") and a.impl == "ours":
+        if rank == 0:
+            {"perc3d": run_perc3d, "serve": run_serve}[a.workload](a)
+        return
     if a.impl == "reference":
         run_reference(a, rank, world)
         return
@@ -555,7 +575,10 @@ def main():
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     try:
-        run_ours(a, rank, world, local)
+        if a.workload == "batch":
+            run_batch(a, rank, world, local)
+        else:
+            run_ours(a, rank, world, local)
     finally:
         if world > 1:
             import torch

@@ -203,6 +203,13 @@ def batch_instance(i, smin=64, smax=1024, p=0.55, sigma=1.0):
     return dims, planes
 
 
+def batch_instance_dims(i, smin=64, smax=1024):
+    """Shape of batch instance i without drawing its conductances (the first
+    draw of the instance's generator, as in batch_instance)."""
+    s = int(rng(SEED_BASE + 1000 * 3 + i).integers(smin, smax + 1))
+    return (s, s)
+
+
 def request_instance(i, p2d=0.52, p3d=0.26):
     """Request i of the served stream: 70 % 2D (side 32..1024), 30 % 3D
     (side 16..128); FBM (H in {0.3,0.5,0.7}, sigma=1) or lognormal (sigma=1),
