@@ -348,21 +348,27 @@ def run_ours(a, rank, world, local):
 
 
 def run_profile_solve(a):
-    """One net_create + one refinement step (one inner CG solve)."""
+    """One net_create + one refinement step (one inner CG solve).  --workload
+    perc3d profiles an n^3 percolation network of the 256^3 workload's kind
+    (n = --size), anything else an n^2 FBM network."""
     import torch
 
     from paper_1908_03301_gb300 import netgen
     from paper_1908_03301_gb300 import netsolve as ns
 
     ns.lib(build_if_missing=True)
-    dims, planes = netgen.workload_fbm2d(n=a.size)
+    if a.workload == "perc3d":
+        dims, planes = netgen.workload_perc3d(n=a.size)
+    else:
+        dims, planes = netgen.workload_fbm2d(n=a.size)
     tplanes = [torch.from_numpy(g).cuda() for g in planes]
     net = ns.Network(dims, tplanes)
     r = net.solve(ns.make_opts(max_outer=1, tol_rel=TOL_REL), check=False)
     net.close()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_solve": True, "size": a.size, "inner_iters": r.inner_iters,
-                      "inner_ms": r.inner_ms, "n_active": r.n_active}), flush=True)
+    print(json.dumps({"profile_solve": True, "dims": list(dims), "inner_iters": r.inner_iters,
+                      "inner_ms": r.inner_ms, "n_active": r.n_active,
+                      "inner_launches": r.inner_launches}), flush=True)
 
 
 # ---------------------------------------------------------------- other workloads

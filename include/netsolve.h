@@ -255,6 +255,43 @@ net_status net_solve_batch(net_t *const *nets, int count, const net_opts *opts,
                            net_result *res);
 
 /*
+ * Autotuner of the CG sweep's tile shape.  Sec. IV picks its launch shape
+ * (64 blocks of 256 threads, a loop over rows per thread) once, by hand, for
+ * the device it used; here the shape is measured on the GPU at hand.
+ *
+ * The sweep kernel (used for 3D networks, FP64 inner loops, 2D networks wider
+ * than 2048 nodes and every batched or queued solve) cuts each network into
+ * segments: blocks of columns (x), in 3D bands of rows (y), each marched
+ * along the last axis.  net_autotune times every candidate shape (column
+ * block width, row band height, segments per SM) with a few CUDA-graph
+ * replays of CG sweeps over the given networks, keeps the fastest in a
+ * process-wide table keyed by (device, dimension, inner precision, size
+ * class = floor(log2(lattice nodes of the set))) and returns it.  Solves of
+ * that key then plan with it.  Solves also tune by themselves the first time
+ * they meet an untuned key (set NETSOLVE_AUTOTUNE=0 to disable; the default
+ * shape is then used), so calling this is optional: it lets a caller tune
+ * ahead of a latency-sensitive run, or re-tune.
+ *   nets    count >= 1 networks on the current device, all 2D or all 3D.
+ *   opts    precision selects the inner loop to tune (NULL = NET_MIXED).
+ *   out     the chosen shape and times (may be NULL).
+ * The networks' inner CG state is overwritten (their pressures are not);
+ * every later net_solve / net_solve_batch starts afresh as always.
+ * NET_EINVAL for mixed dimensions, a NULL network or another device.
+ */
+typedef struct {
+    int col_block;        /* widest column block (nodes along x) */
+    int row_band;         /* tallest row band in 3D (nodes along y); 1 in 2D */
+    int seg_per_sm;       /* segments per SM the march ranges are cut into */
+    int size_class;       /* floor(log2(lattice nodes)) of the key */
+    int candidates;       /* shapes timed */
+    double us_per_sweep;  /* one CG iteration over the set, chosen shape */
+    double us_default;    /* the same with the default shape */
+} net_tune;
+net_status net_autotune(net_t *const *nets, int count, const net_opts *opts, net_tune *out);
+/* Forget every tuned shape (all devices); later solves tune again. */
+void net_tune_clear(void);
+
+/*
  * Continuous-batching queue.  Requests are admitted while their device
  * footprint fits in mem_budget_bytes and a slot among max_slots is free;
  * admitted requests are solved together with those already running, and

@@ -15,6 +15,7 @@
 #include "kernels.h"
 #include "plan.h"
 #include "sweep.cuh"
+#include "tune.h"
 
 namespace netsolve {
 namespace {
@@ -187,15 +188,50 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
     return NET_OK;
 }
 
+net_status BatchEngine::choose_shape(Group &g, PlanShape *shape) {
+    constexpr int kDefaultSeg = 2;
+    *shape = PlanShape{};
+    shape->seg_per_sm = kDefaultSeg;
+    if (tune_forced(g.ndim, g.f32, shape)) return NET_OK;
+    long long nodes = 0;
+    for (BatchItem *it : g.items) nodes += (long long)it->net->g.px * it->net->g.ny * it->net->g.nz;
+    const TuneKey key = tune_key(device_, g.ndim, g.f32, nodes);
+    TuneEntry te;
+    if (tune_lookup(key, &te)) {
+        *shape = te.shape;
+        return NET_OK;
+    }
+    if (tune_enabled() && !g.swept) {
+        std::vector<net_t *> nets;
+        for (BatchItem *it : g.items) nets.push_back(it->net);
+        double bu = 0, du = 0;
+        int nc = 0;
+        net_status s = autotune_nets(nets, g.f32, kDefaultSeg, st_, shape, &bu, &du, &nc);
+        if (s != NET_OK) return s;
+        // the timing sweeps advanced the CG state: arm every network again
+        // from its (unchanged) pressures, exactly as add() did
+        for (BatchItem *it : g.items) {
+            s = outer_pass(it, 0, it->f32);
+            if (s != NET_OK) return s;
+        }
+        return NET_OK;
+    }
+    if (tune_nearest(key, &te)) *shape = te.shape;
+    return NET_OK;
+}
+
 net_status BatchEngine::rebuild(Group &g, int K) {
     if (g.exec) {
         cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
     }
+    PlanShape shape;
+    net_status s0 = choose_shape(g, &shape);
+    if (s0 != NET_OK) return s0;
     std::vector<PlanNet> nets;
     for (BatchItem *it : g.items) nets.push_back(PlanNet{it->net->g, true});
     HostPlan hp;
-    build_plan(nets, g.ndim, g.f32, nsm_, 2, hp);
+    build_plan(nets, g.ndim, g.f32, nsm_, shape, hp);
     size_t tot_part = 0;
     std::vector<SweepInst> si(g.items.size());
     std::vector<size_t> off(g.items.size());
@@ -212,20 +248,9 @@ net_status BatchEngine::rebuild(Group &g, int K) {
     g.d_cta = new_cta;
     CKB(grow(&g.d_part, &g.cap_part, tot_part, st_));
     for (size_t k = 0; k < g.items.size(); k++) {
-        net_t *n = g.items[k]->net;
-        InnerArgs a = inner_args(n, g.f32);
-        SweepInst &s = si[k];
-        s.g = n->g;
-        for (int d = 0; d < 3; d++) s.gs[d] = a.gs[d];
-        s.y = a.y;
-        for (int j = 0; j < 2; j++) {
-            s.r[j] = a.r[j];
-            s.p[j] = a.p[j];
-            s.q[j] = a.q[j];
-        }
-        s.s = a.s;
-        s.part = g.d_part + off[k];
-        s.nseg = hp.nseg[k];
+        si[k] = sweep_inst_of(g.items[k]->net, g.f32);
+        si[k].part = g.d_part + off[k];
+        si[k].nseg = hp.nseg[k];
     }
     CKB(cudaMemcpyAsync(g.d_inst, si.data(), sizeof(SweepInst) * si.size(), cudaMemcpyHostToDevice, st_));
     CKB(cudaMemcpyAsync(g.d_segs, hp.segs.data(), sizeof(SweepSeg) * hp.segs.size(), cudaMemcpyHostToDevice, st_));
@@ -250,6 +275,7 @@ net_status BatchEngine::rebuild(Group &g, int K) {
     g.K = K;
     g.dirty = false;
     g.planned = g.items;
+    g.shape = shape;
     return NET_OK;
 }
 
@@ -278,6 +304,7 @@ net_status BatchEngine::step(int K) {
                 if (s != NET_OK) return s;
             }
             CKB(cudaGraphLaunch(g.exec, st_));
+            g.swept = true;
         }
     // one read of every running network's stop flag and iteration count
     std::vector<BatchItem *> run;
@@ -366,15 +393,18 @@ net_status BatchEngine::step(int K) {
         g64.items.push_back(it);
         g64.dirty = true;
     }
-    // drop finished networks; replan a group once a quarter of it is gone
+    // drop finished networks and replan the group: a sweep lasts as long as
+    // its busiest CTA, and the CTAs that held a finished network's segments
+    // would otherwise idle while the rest keep their full share.  A replan
+    // (host cut, upload, graph instantiation) costs far less than a step.
     for (int d = 0; d < 2; d++)
         for (int f = 0; f < 2; f++) {
             Group &g = groups_[d][f];
             const size_t before = g.items.size();
             g.items.erase(std::remove_if(g.items.begin(), g.items.end(), [](BatchItem *it) { return it->done; }),
                           g.items.end());
-            const size_t gone = before - g.items.size();
-            if (gone && (4 * gone >= before || g.items.size() < 8)) g.dirty = true;
+            if (before != g.items.size()) g.dirty = true;
+            if (g.items.empty()) g.swept = false;
         }
     nrun_ = 0;
     for (int d = 0; d < 2; d++)

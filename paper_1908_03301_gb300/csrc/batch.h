@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "plan.h"
 #include "runtime_internal.h"
 
 namespace netsolve {
@@ -61,6 +62,8 @@ private:
         int grid = 0, K = 0;
         cudaGraphExec_t exec = nullptr;
         std::vector<BatchItem *> planned;  // item order of d_inst
+        bool swept = false;                // a sweep ran since the group was last empty
+        PlanShape shape;                   // tile shape of the current plan
     };
     // A network leaving a group (finished or moved) must not be read by that
     // group's current plan again: its record is pointed at dead_ (stop = 1),
@@ -68,6 +71,10 @@ private:
     // replan.
     void retire(Group &g, BatchItem *it);
     net_status rebuild(Group &g, int K);
+    // Tile shape for the group's next plan: the tuned entry of its key; else,
+    // while no sweep has run on the group (its state is freshly armed), tune
+    // now and re-arm; else the nearest tuned size class; else the default.
+    net_status choose_shape(Group &g, PlanShape *shape);
     net_status outer_pass(BatchItem *it, int apply_corr, int corr_f32);
     void finish(BatchItem *it, net_status st);
     Group &group_of(int ndim, int f32) { return groups_[ndim - 2][f32 ? 1 : 0]; }

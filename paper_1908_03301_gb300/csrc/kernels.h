@@ -68,6 +68,8 @@ struct SweepSeg;
 int sweep_max_width(int ndim, int f32);
 int sweep_vt(int f32);
 int sweep_consumers();
+// Whether a 3D patch of w columns x h rows (plus its halo) fits one stage slot.
+bool sweep_patch_fits(int f32, int w, int h);
 cudaError_t sweep_prepare(int ndim, int f32);
 cudaError_t launch_sweep(int ndim, int f32, int grid, const SweepInst *insts, const SweepSeg *segs,
                          const int *cta_begin, cudaStream_t st);

@@ -1,12 +1,15 @@
 // plan.cu -- host-side work planning for the sweep kernel.
 //
-// Cuts each network into segments (column block x row band x march range,
-// see sweep.cuh) of roughly equal size and deals them to the CTAs (one per
-// SM) longest-first onto the least-loaded CTA, so every SM streams about the
-// same number of bytes per sweep.
+// Every network is cut into bands (column block, and in 3D row band) that
+// are marched along the last axis.  The bands of all networks, in order, form
+// one sequence of march steps; it is cut into equal-cost contiguous pieces,
+// one (or seg_per_sm) per CTA, splitting a band's march range where a piece
+// ends.  A sweep launch waits for its slowest CTA, so equal pieces are what
+// matters: dealing whole, equal segments to CTAs leaves a remainder (e.g. 156
+// segments on 152 SMs run in two rounds).  Each segment costs two extra
+// pipeline-fill steps, which the cut counts.
 #include <algorithm>
 #include <cmath>
-#include <queue>
 #include <vector>
 
 #include "plan.h"
@@ -27,18 +30,100 @@ static std::vector<int> split(int n, int parts) {
     return w;
 }
 
-void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, int seg_per_sm,
+bool plan_shape_valid(int ndim, int f32, const PlanShape &shape) {
+    const int wmax = sweep_max_width(ndim, f32);
+    const int cap = sweep_consumers() * sweep_vt(f32);
+    if (shape.seg_per_sm < 1 || shape.seg_per_sm > 64) return false;
+    if (shape.wcap != 0 && (shape.wcap < 4 || shape.wcap % 4 || shape.wcap > wmax)) return false;
+    if (shape.hcap < 0 || shape.hcap > 32) return false;
+    if (ndim == 3 && shape.hcap > 0) {
+        const int w = shape.wcap > 0 ? shape.wcap : wmax;
+        if ((long long)w * shape.hcap > cap) return false;
+        if (!sweep_patch_fits(f32, w, shape.hcap)) return false;
+    }
+    return true;
+}
+
+namespace {
+
+// A band: one column block (and in 3D one row band) of one network, marched
+// along the last axis; each march step touches w*h nodes.
+struct Band {
+    int inst, x0, w, y0, h, nm;
+};
+
+// Cost of a segment of L march steps of band b: its steps plus the two
+// pipeline-fill steps that load the planes on either side.
+inline double seg_cost(const Band &b, long long L) { return (double)b.w * b.h * (double)(L + 2); }
+
+// Greedy cut of the band sequence into pieces of cost <= T (a segment is
+// never shorter than `min_steps` unless its band is).  Returns the number of
+// pieces; fills `out` (piece index per segment) when non-null.
+int greedy_cut(const std::vector<Band> &bands, double T, int min_steps, std::vector<SweepSeg> *segs,
+               std::vector<int> *piece) {
+    int np = 0;
+    double load = 0.0;
+    bool open = false;
+    for (const Band &b : bands) {
+        int m = 0;
+        while (m < b.nm) {
+            const int rem = b.nm - m;
+            long long fit = (long long)((T - load) / ((double)b.w * b.h)) - 2;
+            int take;
+            if (fit >= rem) {
+                take = rem;
+            } else if (fit >= min_steps || (!open && fit >= 1)) {
+                take = (int)fit;
+                if (rem - take < min_steps) take = std::max(1, rem - min_steps);  // no stub after it
+            } else if (open) {
+                np++;  // close the current piece, retry in a fresh one
+                load = 0.0;
+                open = false;
+                continue;
+            } else {
+                take = std::min(rem, min_steps);  // a piece must make progress
+            }
+            if (segs) {
+                SweepSeg sg;
+                sg.inst = b.inst;
+                sg.x0 = b.x0;
+                sg.w = b.w;
+                sg.y0 = b.y0;
+                sg.h = b.h;
+                sg.m0 = m;
+                sg.m1 = m + take;
+                sg.slot = 0;
+                segs->push_back(sg);
+                piece->push_back(np);
+            }
+            load += seg_cost(b, take);
+            open = true;
+            m += take;
+            if (load >= T * 0.999) {
+                np++;
+                load = 0.0;
+                open = false;
+            }
+        }
+    }
+    return np + (open ? 1 : 0);
+}
+
+}  // namespace
+
+void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, const PlanShape &shape,
                 HostPlan &out) {
     out.segs.clear();
     out.nseg.assign(nets.size(), 0);
-    const int wmax = sweep_max_width(ndim, f32);
+    const int wmax = shape.wcap > 0 ? std::min(shape.wcap, sweep_max_width(ndim, f32))
+                                    : sweep_max_width(ndim, f32);
+    const int hlim = shape.hcap > 0 ? shape.hcap : 32;
     const int cap = sweep_consumers() * sweep_vt(f32);  // elements per step
-    long long tot = 0;
-    for (const PlanNet &pn : nets)
-        if (pn.active) tot += (long long)pn.g.px * pn.g.ny * pn.g.nz;
-    const double target = std::max(1.0, (double)tot / ((double)nsm * std::max(1, seg_per_sm)));
-    std::vector<SweepSeg> all;
-    std::vector<double> cost;
+    const int grid = std::max(1, nsm);
+    const int P = grid * std::max(1, shape.seg_per_sm);  // pieces
+    // bands in network order
+    std::vector<Band> bands;
+    double total = 0.0, biggest = 0.0;
     for (size_t k = 0; k < nets.size(); k++) {
         const PlanNet &pn = nets[k];
         if (!pn.active) continue;
@@ -46,14 +131,12 @@ void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, in
         const int kb = (g.px + wmax - 1) / wmax;
         const std::vector<int> ws = split4(g.px, kb);
         int x0 = 0;
-        int slot = 0;
         for (int bx = 0; bx < kb; bx++) {
             const int w = ws[bx];
-            std::vector<int> hs{1};
-            std::vector<int> y0s{0};
+            std::vector<int> hs{1}, y0s{0};
             int nm = g.ny;
             if (ndim == 3) {
-                const int hmax = std::max(1, std::min({32, cap / std::max(w, 1), g.ny}));
+                const int hmax = std::max(1, std::min({hlim, cap / std::max(w, 1), g.ny}));
                 const int yb = (g.ny + hmax - 1) / hmax;
                 hs = split(g.ny, yb);
                 y0s.assign(yb, 0);
@@ -61,49 +144,32 @@ void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, in
                 nm = g.nz;
             }
             for (size_t j = 0; j < hs.size(); j++) {
-                const double nodes = (double)w * hs[j] * nm;
-                int R = (int)std::lround(nodes / target);
-                R = std::max(1, std::min(R, std::max(1, nm / 4)));
-                const std::vector<int> ms = split(nm, R);
-                int m0 = 0;
-                for (int rI = 0; rI < R; rI++) {
-                    SweepSeg sg;
-                    sg.inst = (int)k;
-                    sg.x0 = x0;
-                    sg.w = w;
-                    sg.y0 = y0s[j];
-                    sg.h = hs[j];
-                    sg.m0 = m0;
-                    sg.m1 = m0 + ms[rI];
-                    sg.slot = slot++;
-                    m0 = sg.m1;
-                    all.push_back(sg);
-                    cost.push_back((double)w * hs[j] * (ms[rI] + 2) + 2.0 * w * 2 * (ndim == 3 ? ms[rI] : 0));
-                }
+                Band b{(int)k, x0, w, y0s[j], hs[j], nm};
+                bands.push_back(b);
+                total += seg_cost(b, nm);
+                biggest = std::max(biggest, (double)b.w * b.h * 4.0);
             }
             x0 += w;
         }
-        out.nseg[k] = slot;
     }
-    // longest first onto the least-loaded CTA
-    const int grid = std::max(1, nsm);
-    std::vector<int> order(all.size());
-    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    using Item = std::pair<double, int>;
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-    for (int c = 0; c < grid; c++) heap.push({0.0, c});
+    // smallest bottleneck cost T with at most P pieces (binary search on T)
+    const int min_steps = 4;
+    double lo = std::max(total / P, biggest), hi = std::max(total, lo) * 1.01 + 1.0;
+    for (int it = 0; it < 40 && hi - lo > 1e-4 * lo; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy_cut(bands, mid, min_steps, nullptr, nullptr) <= P) hi = mid;
+        else lo = mid;
+    }
+    std::vector<SweepSeg> all;
+    std::vector<int> piece;
+    greedy_cut(bands, hi, min_steps, &all, &piece);
+    // slots: order of each network's segments
+    for (SweepSeg &sg : all) sg.slot = out.nseg[sg.inst]++;
+    // piece p -> CTA p % grid, pieces in order inside a CTA
     std::vector<std::vector<int>> lists(grid);
-    for (int i : order) {
-        Item it = heap.top();
-        heap.pop();
-        lists[it.second].push_back(i);
-        it.first += cost[i];
-        heap.push(it);
-    }
+    for (size_t i = 0; i < all.size(); i++) lists[std::min(piece[i], P - 1) % grid].push_back((int)i);
     out.cta_begin.assign(grid + 1, 0);
     for (int c = 0; c < grid; c++) {
-        std::sort(lists[c].begin(), lists[c].end());  // network-major order inside a CTA
         out.cta_begin[c + 1] = out.cta_begin[c] + (int)lists[c].size();
         for (int i : lists[c]) out.segs.push_back(all[i]);
     }

@@ -22,6 +22,7 @@
 #include "kernels.h"
 #include "plan.h"
 #include "runtime_internal.h"
+#include "tune.h"
 
 using namespace netsolve;
 
@@ -154,6 +155,13 @@ struct DevGuard {
 
 }  // namespace
 
+int netsolve::device_sm_count(int dev) {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        nsm = 152;
+    return nsm;
+}
+
 net_status netsolve::ensure_precision(net_t *n, int f32, cudaStream_t st) {
     const int k = f32 ? 0 : 1;
     const size_t L = (size_t)n->g.len;
@@ -198,38 +206,30 @@ net_status ensure_persist(net_t *n) {
     return NET_OK;
 }
 
-int device_sm_count(int dev) {
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-        nsm = 152;
-    return nsm;
-}
-
-// Plan the sweep for this one network and upload it (per precision).
-net_status ensure_sweep_plan(net_t *n, int f32) {
+// Plan the sweep for this one network with a tile shape and upload it (per
+// precision); an existing plan of another shape is replaced.
+net_status ensure_sweep_plan(net_t *n, int f32, const PlanShape &shape) {
     const int k = f32 ? 0 : 1;
-    if (n->sw[k].segs) return NET_OK;
+    SweepDev &sd = n->sw[k];
+    if (sd.segs && same_shape(sd.shape, shape)) return NET_OK;
     cudaStream_t st = n->stream;
+    if (sd.segs) {
+        dfree(sd.segs, st);
+        dfree(sd.cta, st);
+        dfree(sd.part, st);
+        dfree(sd.inst, st);
+        sd = SweepDev{};
+    }
     HostPlan hp;
     std::vector<PlanNet> nets{PlanNet{n->g, true}};
-    build_plan(nets, n->g.ndim, f32, device_sm_count(n->device), 1, hp);
-    SweepDev &sd = n->sw[k];
+    build_plan(nets, n->g.ndim, f32, device_sm_count(n->device), shape, hp);
     sd.grid = hp.grid;
+    sd.shape = shape;
     CK(dalloc(&sd.segs, sizeof(SweepSeg) * hp.segs.size(), st));
     CK(dalloc(&sd.cta, sizeof(int) * hp.cta_begin.size(), st));
     CK(dalloc(&sd.part, sizeof(double) * 4 * (size_t)std::max(1, hp.nseg[0]), st));
     CK(dalloc(&sd.inst, sizeof(SweepInst), st));
-    InnerArgs a = inner_args(n, f32);
-    SweepInst si{};
-    si.g = n->g;
-    for (int d = 0; d < 3; d++) si.gs[d] = a.gs[d];
-    si.y = a.y;
-    for (int j = 0; j < 2; j++) {
-        si.r[j] = a.r[j];
-        si.p[j] = a.p[j];
-        si.q[j] = a.q[j];
-    }
-    si.s = a.s;
+    SweepInst si = sweep_inst_of(n, f32);
     si.part = sd.part;
     si.nseg = hp.nseg[0];
     CK(cudaMemcpyAsync(sd.segs, hp.segs.data(), sizeof(SweepSeg) * hp.segs.size(), cudaMemcpyHostToDevice, st));
@@ -239,17 +239,42 @@ net_status ensure_sweep_plan(net_t *n, int f32) {
     return NET_OK;
 }
 
+// Tile shape for a single network's sweep plan: the tuned entry of its key,
+// else tune now (before the solve arms its state), else the default.
+net_status sweep_shape_for(net_t *n, int f32, PlanShape *shape) {
+    *shape = PlanShape{};
+    const Geom &G = n->g;
+    if (tune_forced(G.ndim, f32, shape)) return NET_OK;
+    const TuneKey key = tune_key(n->device, G.ndim, f32, (long long)G.px * G.ny * G.nz);
+    TuneEntry te;
+    if (tune_lookup(key, &te)) {
+        *shape = te.shape;
+        return NET_OK;
+    }
+    if (!tune_enabled() || n->n_active == 0) return NET_OK;
+    double best_us = 0, def_us = 0;
+    int nc = 0;
+    std::vector<net_t *> one{n};
+    return autotune_nets(one, f32, 1, n->stream, shape, &best_us, &def_us, &nc);
+}
+
 net_status ensure_graph(net_t *n, int f32, int K) {
     const int k = f32 ? 0 : 1;
-    if (n->gexec[k] && n->gk[k] == K) return NET_OK;
+    const bool sweep = use_sweep_kernel();
+    PlanShape shape;
+    if (sweep) {
+        net_status s = sweep_shape_for(n, f32, &shape);
+        if (s != NET_OK) return s;
+    }
+    if (n->gexec[k] && n->gk[k] == K && (!sweep || (n->sw[k].segs && same_shape(n->sw[k].shape, shape))))
+        return NET_OK;
     if (n->gexec[k]) {
         cudaGraphExecDestroy(n->gexec[k]);
         n->gexec[k] = nullptr;
     }
     InnerArgs a = inner_args(n, f32);
-    const bool sweep = use_sweep_kernel();
     if (sweep) {
-        net_status s = ensure_sweep_plan(n, f32);
+        net_status s = ensure_sweep_plan(n, f32, shape);
         if (s != NET_OK) return s;
         CK(sweep_prepare(n->g.ndim, f32));
     }
@@ -339,6 +364,98 @@ OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_
     o.stag_window = f32 && !rel_mode ? std::max(400LL, 8LL * side) : std::max(4000LL, 64LL * side);
     o.partials = n->partials;
     return o;
+}
+
+SweepInst sweep_inst_of(net_t *n, int f32) {
+    InnerArgs a = inner_args(n, f32);
+    SweepInst si{};
+    si.g = n->g;
+    for (int d = 0; d < 3; d++) si.gs[d] = a.gs[d];
+    si.y = a.y;
+    for (int j = 0; j < 2; j++) {
+        si.r[j] = a.r[j];
+        si.p[j] = a.p[j];
+        si.q[j] = a.q[j];
+    }
+    si.s = a.s;
+    si.part = nullptr;
+    si.nseg = 0;
+    return si;
+}
+
+net_status arm_for_tuning(net_t *n, int f32, cudaStream_t st) {
+    net_opts o;
+    net_opts_default(&o);
+    o.refine = NET_REFINE_RESTART;
+    OuterArgs oa = outer_args(n, f32, 0, f32, o, 0);
+    oa.tol_rel = 0.0;
+    oa.tol_geff = 0.0;
+    oa.tol_floor = 0.0;
+    oa.reliable = 0;
+    oa.allow_cont = 0;
+    oa.delta2 = 0.0;
+    CK(launch_outer(oa, st));
+    return NET_OK;
+}
+
+net_status autotune_nets(const std::vector<net_t *> &nets, int f32, int default_seg, cudaStream_t st,
+                         PlanShape *best, double *best_us, double *def_us, int *ncand) {
+    *best = PlanShape{};
+    best->seg_per_sm = default_seg;
+    *best_us = *def_us = 0.0;
+    *ncand = 0;
+    if (nets.empty()) return NET_OK;
+    const int ndim = nets[0]->g.ndim, dev = nets[0]->device;
+    long long nodes = 0;
+    std::vector<PlanNet> pn;
+    std::vector<SweepInst> si;
+    for (net_t *n : nets) {
+        if (n->g.ndim != ndim || n->device != dev) {
+            set_error("autotune: networks differ in dimension or device");
+            return NET_EINVAL;
+        }
+        if (n->stream != st) {  // the network's own stream may still hold its set-up work
+            CK(cudaEventRecord(n->ev[3], n->stream));
+            CK(cudaStreamWaitEvent(st, n->ev[3], 0));
+        }
+        net_status s = ensure_precision(n, f32, st);
+        if (s != NET_OK) return s;
+        nodes += (long long)n->g.px * n->g.ny * n->g.nz;
+        pn.push_back(PlanNet{n->g, true});
+        si.push_back(sweep_inst_of(n, f32));
+    }
+    const std::vector<PlanShape> cands = tune_candidates(ndim, f32, default_seg);
+    const int nsm = device_sm_count(dev);
+    // 8 sweeps per graph, 3 timed replays after one warm replay: every
+    // candidate starts from the same freshly armed state
+    const int K = 8, R = 3;
+    double bu = -1.0;
+    for (size_t c = 0; c < cands.size(); c++) {
+        for (net_t *n : nets) {
+            net_status s = arm_for_tuning(n, f32, st);
+            if (s != NET_OK) return s;
+        }
+        const double us = tune_time_shape(pn, si, ndim, f32, nsm, cands[c], K, R, st);
+        if (us < 0.0) return NET_ECUDA;
+        if (c == 0) *def_us = us;
+        // a candidate must beat the best so far by 2 % (timing noise)
+        if (bu < 0.0 || us < 0.98 * bu) {
+            bu = us;
+            *best = cands[c];
+        }
+    }
+    *best_us = bu;
+    *ncand = (int)cands.size();
+    TuneEntry te;
+    te.shape = *best;
+    te.us_per_sweep = bu;
+    te.candidates = *ncand;
+    tune_store(tune_key(dev, ndim, f32, nodes), te);
+    if (trace_on())
+        fprintf(stderr, "[trace autotune] %dD %s nets %zu nodes %lld: wcap %d hcap %d seg %d %.2f us (default %.2f)\n",
+                ndim, f32 ? "f32" : "f64", nets.size(), nodes, best->wcap, best->hcap, best->seg_per_sm, bu,
+                *def_us);
+    return NET_OK;
 }
 
 // Outer correction with y of one precision but the residual written for
@@ -665,6 +782,54 @@ NET_API void net_opts_default(net_opts *o) {
     o->refine = NET_REFINE_RELIABLE;
     o->update_delta = 1e-3;
 }
+
+NET_API net_status net_autotune(net_t *const *nets, int count, const net_opts *opts, net_tune *out) {
+    if (count < 1 || !nets) {
+        set_error("net_autotune: no networks");
+        return NET_EINVAL;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<net_t *> v;
+    for (int i = 0; i < count; i++) {
+        if (!nets[i] || nets[i]->device != dev) {
+            set_error("net_autotune: network %d is NULL or on another device", i);
+            return NET_EINVAL;
+        }
+        if (nets[i]->g.ndim != nets[0]->g.ndim) {
+            set_error("net_autotune: networks mix 2D and 3D");
+            return NET_EINVAL;
+        }
+        v.push_back(nets[i]);
+    }
+    const int f32 = !opts || opts->precision == NET_MIXED;
+    cudaStream_t st = opts && opts->stream ? (cudaStream_t)opts->stream : nets[0]->stream;
+    PlanShape best;
+    double bu = 0, du = 0;
+    int nc = 0;
+    // a set of one network is planned as net_solve plans it (one segment per
+    // SM by default), a larger set as net_solve_batch does (two)
+    net_status s = autotune_nets(v, f32, count == 1 ? 1 : 2, st, &best, &bu, &du, &nc);
+    if (s != NET_OK) return s;
+    if (out) {
+        long long nodes = 0;
+        for (net_t *n : v) nodes += (long long)n->g.px * n->g.ny * n->g.nz;
+        const int ndim = v[0]->g.ndim;
+        const int wmax = sweep_max_width(ndim, f32);
+        const int w = best.wcap > 0 ? best.wcap : wmax;
+        const int cap = sweep_consumers() * sweep_vt(f32);
+        out->col_block = w;
+        out->row_band = ndim == 3 ? std::min(best.hcap > 0 ? best.hcap : 32, cap / w) : 1;
+        out->seg_per_sm = best.seg_per_sm;
+        out->size_class = tune_key(dev, ndim, f32, nodes).size_class;
+        out->candidates = nc;
+        out->us_per_sweep = bu;
+        out->us_default = du;
+    }
+    return NET_OK;
+}
+
+NET_API void net_tune_clear(void) { tune_clear(); }
 
 NET_API net_status net_create(const net_desc *desc, const void *const g[3], net_t **out) {
     return create_network(desc, g, out);

@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
 
 #include "../../include/netsolve.h"
 #include "kernels.h"
+#include "plan.h"
 #include "sweep.cuh"
 
 namespace netsolve {
@@ -17,7 +19,11 @@ struct SweepDev {
     double *part = nullptr;
     SweepInst *inst = nullptr;
     int grid = 0;
+    PlanShape shape;  // tile shape the plan was built with
 };
+inline bool same_shape(const PlanShape &a, const PlanShape &b) {
+    return a.wcap == b.wcap && a.hcap == b.hcap && a.seg_per_sm == b.seg_per_sm;
+}
 
 // Device-resident scalars of one network (one allocation).
 struct DevScal {
@@ -131,4 +137,16 @@ net_status setup_network(net_t *n, const void *const g[3], int on_device);
 void release_network(net_t *n);
 net_status create_network(const net_desc *desc, const void *const g[3], net_t **out);
 net_status solve_impl(net_t *n, const net_opts *o, net_result *r);
+// Arm a network's inner state of one precision for timing sweeps: a fresh CG
+// from the current pressures that stops only on an exactly zero residual.
+// The next solve (or batch add) re-arms it for real.
+net_status arm_for_tuning(net_t *n, int f32, cudaStream_t st);
+// Sweep record of one network for a plan (part / nseg filled by the planner).
+SweepInst sweep_inst_of(net_t *n, int f32);
+int device_sm_count(int dev);
+// Tune the sweep tile shape over these networks (same dimension, inner
+// precision f32) and store the winner under their key.  Their inner state is
+// left armed for tuning.  *def_us gets the default shape's time.
+net_status autotune_nets(const std::vector<net_t *> &nets, int f32, int default_seg, cudaStream_t st,
+                         PlanShape *best, double *best_us, double *def_us, int *ncand);
 }  // namespace netsolve

@@ -672,6 +672,11 @@ int sweep_max_width(int ndim, int f32) {
     return f32 ? SW<float, 3>::WMAX : SW<double, 3>::WMAX;
 }
 int sweep_vt(int f32) { return f32 ? 2 : 1; }
+bool sweep_patch_fits(int f32, int w, int h) {
+    const long long es = f32 ? 4 : 8, V = 16 / es;
+    const long long need = (long long)(h + 2) * (w + 2 * V) * es;
+    return need <= (f32 ? SW<float, 3>::SLOT : SW<double, 3>::SLOT);
+}
 int sweep_consumers() { return NC; }
 
 cudaError_t sweep_prepare(int ndim, int f32) {

@@ -49,10 +49,19 @@ class net_result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class net_tune(C.Structure):
+    _fields_ = [("col_block", C.c_int), ("row_band", C.c_int), ("seg_per_sm", C.c_int),
+                ("size_class", C.c_int), ("candidates", C.c_int), ("us_per_sweep", C.c_double),
+                ("us_default", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_pressure",
            "net_get_labels", "net_destroy", "net_solve_batch", "netq_create", "netq_submit",
            "netq_poll", "netq_wait", "netq_cancel", "netq_stats", "netq_destroy",
-           "net_last_error", "net_labels_noalloc"]
+           "net_last_error", "net_labels_noalloc", "net_autotune", "net_tune_clear"]
 
 _lib = None
 
@@ -88,6 +97,10 @@ def lib(build_if_missing: bool = False):
     L.net_last_error.restype = C.c_char_p
     L.net_labels_noalloc.argtypes = [P(net_desc), P(vp), vp, vp]
     L.net_labels_noalloc.restype = C.c_int
+    L.net_autotune.argtypes = [P(vp), C.c_int, P(net_opts), P(net_tune)]
+    L.net_autotune.restype = C.c_int
+    L.net_tune_clear.argtypes = []
+    L.net_tune_clear.restype = None
     L.net_solve_batch.argtypes = [P(vp), C.c_int, P(net_opts), P(net_result)]
     L.net_solve_batch.restype = C.c_int
     L.netq_create.argtypes = [C.c_size_t, C.c_int, P(net_opts), P(vp)]
@@ -302,6 +315,22 @@ def solve_batch(networks, opts: net_opts | None = None, check=True):
     if check and st not in (NET_OK, NET_ENOTCONVERGED):
         raise NetError(st, "net_solve_batch")
     return [Result.from_c(res[i]) for i in range(n)]
+
+
+def autotune(networks, opts: net_opts | None = None) -> dict:
+    """net_autotune over a list of Network objects (all 2D or all 3D); returns
+    the chosen tile shape and its time per sweep as a dict."""
+    n = len(networks)
+    hs = (C.c_void_p * n)(*[net.h for net in networks])
+    out = net_tune()
+    _check(lib().net_autotune(hs, n, C.byref(opts) if opts is not None else None, C.byref(out)),
+           "net_autotune")
+    return out.as_dict()
+
+
+def tune_clear():
+    """net_tune_clear: forget every tuned tile shape."""
+    lib().net_tune_clear()
 
 
 class Queue:

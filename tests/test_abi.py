@@ -62,14 +62,17 @@ def test_host_side_validation_without_gpu(so):
     assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
     assert L.net_solve(None, None, None) == ns.NET_EINVAL
     assert L.net_destroy(None) == ns.NET_OK
+    assert L.net_autotune(None, 0, None, None) == ns.NET_EINVAL
+    L.net_tune_clear()
 
 
 def test_struct_layouts_match_header(tmp_path):
-    """The ctypes mirrors of net_desc, net_opts and net_result have the
-    header's field offsets and sizes (compiled with the host C compiler)."""
+    """The ctypes mirrors of net_desc, net_opts, net_result and net_tune have
+    the header's field offsets and sizes (compiled with the host C compiler)."""
     from paper_1908_03301_gb300 import netsolve as ns
 
-    structs = {"net_desc": ns.net_desc, "net_opts": ns.net_opts, "net_result": ns.net_result}
+    structs = {"net_desc": ns.net_desc, "net_opts": ns.net_opts, "net_result": ns.net_result,
+               "net_tune": ns.net_tune}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "netsolve.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
