@@ -47,14 +47,27 @@ bool plan_shape_valid(int ndim, int f32, const PlanShape &shape) {
 namespace {
 
 // A band: one column block (and in 3D one row band) of one network, marched
-// along the last axis; each march step touches w*h nodes.
+// along the last axis; each march step touches w*h nodes.  `step` is the
+// modelled cost of one march step in node-equivalents.
 struct Band {
     int inst, x0, w, y0, h, nm;
+    double step;
 };
+
+// A march step costs its nodes plus a fixed amount per bulk copy it issues
+// (measured on GB300: about 0.1 us of the producer's time per copy, the time
+// about 100 nodes' worth of bytes take at an SM's share of HBM bandwidth).
+// 2D steps copy 6 rows; 3D steps over whole padded rows copy each array once
+// (7 copies), narrower 3D patches copy row by row.
+constexpr double kCopyCost = 100.0;
+inline double step_cost(int ndim, int w, int h, bool full_rows) {
+    const int copies = ndim == 2 ? 6 : (full_rows ? 7 : 3 * (h + 2) + 4 * h + 1);
+    return (double)w * h + kCopyCost * copies;
+}
 
 // Cost of a segment of L march steps of band b: its steps plus the two
 // pipeline-fill steps that load the planes on either side.
-inline double seg_cost(const Band &b, long long L) { return (double)b.w * b.h * (double)(L + 2); }
+inline double seg_cost(const Band &b, long long L) { return b.step * (double)(L + 2); }
 
 // Greedy cut of the band sequence into pieces of cost <= T (a segment is
 // never shorter than `min_steps` unless its band is).  Returns the number of
@@ -68,7 +81,7 @@ int greedy_cut(const std::vector<Band> &bands, double T, int min_steps, std::vec
         int m = 0;
         while (m < b.nm) {
             const int rem = b.nm - m;
-            long long fit = (long long)((T - load) / ((double)b.w * b.h)) - 2;
+            long long fit = (long long)((T - load) / b.step) - 2;
             int take;
             if (fit >= rem) {
                 take = rem;
@@ -144,10 +157,11 @@ void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, co
                 nm = g.nz;
             }
             for (size_t j = 0; j < hs.size(); j++) {
-                Band b{(int)k, x0, w, y0s[j], hs[j], nm};
+                const bool full_rows = ndim == 3 && kb == 1;
+                Band b{(int)k, x0, w, y0s[j], hs[j], nm, step_cost(ndim, w, hs[j], full_rows)};
                 bands.push_back(b);
                 total += seg_cost(b, nm);
-                biggest = std::max(biggest, (double)b.w * b.h * 4.0);
+                biggest = std::max(biggest, b.step * 4.0);
             }
             x0 += w;
         }

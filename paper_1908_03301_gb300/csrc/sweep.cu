@@ -119,6 +119,8 @@ struct ProdSeg {
     long long ms;                            // march stride (elements)
     long long rs;                            // row stride within a 3D patch
     int nm, m0, m1, w, h;
+    int px;     // row pitch
+    bool full;  // 3D patch spanning whole padded rows: its rows are contiguous
     bool first;
 };
 
@@ -141,13 +143,44 @@ __device__ __forceinline__ void produce_step(unsigned char *smem, uint64_t *full
     const uint32_t bw = (uint32_t)(w + 2 * V) * sizeof(T), bn = (uint32_t)w * sizeof(T),
                    bx = (uint32_t)(w + V) * sizeof(T);
     const int total = nL * rowsL + nY + nGX + nGY + nGZ;
+    const long long oe = (long long)me * ps.ms, ot = (long long)mt * ps.ms;
+    // exactly one arrive.expect_tx per stage and step (the full barrier
+    // counts one arrival): whole-row patches take their own branch
+    if (NDIM == 3 && ps.full) {
+        // whole rows: each array's rows are one contiguous run, so one copy
+        // per array (the row ends' zero bonds stand in for halo columns)
+        const int px = ps.px;
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)nL * (uint32_t)(rowsL * px + 2 * V) * sizeof(T) +
+                                   (uint32_t)(nY ? h * px : 0) * sizeof(T) +
+                                   (uint32_t)(nGX ? h * px + V : 0) * sizeof(T) +
+                                   (uint32_t)(nGY ? (h + 1) * px : 0) * sizeof(T) +
+                                   (uint32_t)(nGZ ? h * px : 0) * sizeof(T);
+            mbar_arrive_expect_tx(&full[b], bytes);
+        }
+        __syncwarp();
+        if (lane < nL) {
+            const T *src = lane == 0 ? ps.r : (lane == 1 ? ps.q : ps.p);
+            bulk_load(stage_arr<T, NDIM>(smem, b, lane), src + oe - (long long)HH * ps.rs,
+                      (uint32_t)(rowsL * px + 2 * V) * sizeof(T), &full[b]);
+        } else if (lane == 4 && nY) {
+            bulk_load(stage_arr<T, NDIM>(smem, b, A_Y), ps.y + oe, (uint32_t)(h * px) * sizeof(T), &full[b]);
+        } else if (lane == 5 && nGX) {
+            bulk_load(stage_arr<T, NDIM>(smem, b, A_GX), ps.gx + ot, (uint32_t)(h * px + V) * sizeof(T), &full[b]);
+        } else if (lane == 6 && nGY) {
+            bulk_load(stage_arr<T, NDIM>(smem, b, A_GY), ps.gy + ot - ps.rs, (uint32_t)((h + 1) * px) * sizeof(T),
+                      &full[b]);
+        } else if (lane == 7 && nGZ) {
+            bulk_load(stage_arr<T, NDIM>(smem, b, A_GZ), ps.gz + ot, (uint32_t)(h * px) * sizeof(T), &full[b]);
+        }
+        return;
+    }
     if (lane == 0) {
         const uint32_t bytes = (uint32_t)(nL * rowsL) * bw + (uint32_t)nY * bn + (uint32_t)nGX * bx +
                                (uint32_t)(nGY + nGZ) * bn;
         mbar_arrive_expect_tx(&full[b], bytes);
     }
     __syncwarp();
-    const long long oe = (long long)me * ps.ms, ot = (long long)mt * ps.ms;
     for (int k = lane; k < total; k += 32) {
         int kk = k;
         if (kk < nL * rowsL) {
@@ -387,6 +420,8 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
             ps.m1 = sv.m1;
             ps.w = sv.w;
             ps.h = sv.h;
+            ps.px = g.px;
+            ps.full = NDIM == 3 && sv.x0 == 0 && sv.w == g.px;
             ps.first = sv.first;
             for (int t = -2; t < sv.m1 - sv.m0; t++, G++) {
                 const int b = (int)(G % S);
@@ -422,7 +457,11 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
         const T alpha = (T)I.s->alpha, beta = (T)I.s->beta;
         const bool first = sv.first;
         const int w = sv.w, h = sv.h, nv = sv.nv;
-        const int PW = w + 2 * V;
+        // whole-row patches are staged as contiguous runs (row pitch px, the
+        // halo columns are the neighbouring rows' ends, whose bonds are 0)
+        const bool fullw = NDIM == 3 && sv.x0 == 0 && w == px;
+        const int PW = fullw ? px : w + 2 * V;
+        const int GXW = fullw ? px : w + V;
         const bool own = c < sv.nitems;
         const int rr = own ? c / nv : 0, vv = own ? c % nv : 0;
         // this thread's element at march index m is base + m * ms
@@ -433,7 +472,7 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
         T *yv = (T *)I.y + base;
         const int o_own = (rr + HH) * PW + V + vv * VT;  // ring / r q p offset
         const int o_y = rr * w + vv * VT;
-        const int o_gx = rr * (w + V) + V + vv * VT;
+        const int o_gx = rr * GXW + V + vv * VT;
         const int o_gz = rr * w + vv * VT;
         const int y0 = sv.y0, x0 = sv.x0;
         V8<T> r_next, r_cur, mdown;
@@ -515,7 +554,7 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
                         pn.st(ring + o);
                     }
                 }
-                for (int j = c; j < 2 * h; j += NC) {  // halo columns x0-1, x0+w
+                for (int j = c; !fullw && j < 2 * h; j += NC) {  // halo columns x0-1, x0+w
                     const int side = j & 1, hr = j >> 1;
                     const int col = side ? w : -1, x = x0 + col;
                     const int o = (hr + HH) * PW + V + col;
@@ -536,7 +575,7 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
                         z.zero();
                         z.st(ring + ((j < nv ? -1 : h) + HH) * PW + V + (j % nv) * VT);
                     }
-                for (int j = c; j < 2 * h; j += NC) ring[((j >> 1) + HH) * PW + V + ((j & 1) ? w : -1)] = T(0);
+                for (int j = c; !fullw && j < 2 * h; j += NC) ring[((j >> 1) + HH) * PW + V + ((j & 1) ? w : -1)] = T(0);
                 r_next.zero();
             }
             cons_sync();

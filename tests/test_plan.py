@@ -76,7 +76,8 @@ def check_plan(plan, ndim, dims_list, f32=1, slack=1.30):
             cover[inst][0, m0:m1, x0:x0 + w] += 1
         assert slot not in slots[inst]
         slots[inst].add(slot)
-        load[cta] += w * h * (m1 - m0 + 2)
+        copies = 6 if ndim == 2 else (7 if w == (dims_list[inst][0] + 3) // 4 * 4 else 3 * (h + 2) + 4 * h + 1)
+        load[cta] += (w * h + 100 * copies) * (m1 - m0 + 2)
     for k, c in enumerate(cover):
         assert (c == 1).all(), f"network {k}: nodes covered {c.min()}..{c.max()} times"
         assert slots[k] == set(range(nseg[k]))
