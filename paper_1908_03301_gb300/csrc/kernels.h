@@ -68,6 +68,8 @@ struct SweepSeg;
 int sweep_max_width(int ndim, int f32);
 int sweep_vt(int f32);
 int sweep_consumers();
+// Rows a 2D segment stages per pipeline step (1 in 3D).
+int sweep_rows_per_stage(int ndim, int f32, int w, int px, int x0);
 // Whether a 3D patch of w columns x h rows (plus its halo) fits one stage slot.
 bool sweep_patch_fits(int f32, int w, int h);
 cudaError_t sweep_prepare(int ndim, int f32);

@@ -55,13 +55,15 @@ struct Band {
 };
 
 // A march step costs its nodes plus a fixed amount per bulk copy it issues
-// (measured on GB300: about 0.1 us of the producer's time per copy, the time
-// about 100 nodes' worth of bytes take at an SM's share of HBM bandwidth).
-// 2D steps copy 6 rows; 3D steps over whole padded rows copy each array once
-// (7 copies), narrower 3D patches copy row by row.
+// (measured on GB300: about 0.1 us of the copy engine's time per copy, the
+// time about 100 nodes' worth of bytes take at an SM's share of HBM
+// bandwidth).  2D steps stage `rows` rows together: 6 copies per stage over
+// whole rows, 6 per row otherwise; 3D steps over whole padded rows copy each
+// array once (7 copies), narrower 3D patches copy row by row.
 constexpr double kCopyCost = 100.0;
-inline double step_cost(int ndim, int w, int h, bool full_rows) {
-    const int copies = ndim == 2 ? 6 : (full_rows ? 7 : 3 * (h + 2) + 4 * h + 1);
+inline double step_cost(int ndim, int w, int h, bool full_rows, int rows) {
+    const double copies = ndim == 2 ? (full_rows ? 6.0 / rows : 6.0)
+                                    : (full_rows ? 7.0 : 3.0 * (h + 2) + 4.0 * h + 1.0);
     return (double)w * h + kCopyCost * copies;
 }
 
@@ -157,8 +159,9 @@ void build_plan(const std::vector<PlanNet> &nets, int ndim, int f32, int nsm, co
                 nm = g.nz;
             }
             for (size_t j = 0; j < hs.size(); j++) {
-                const bool full_rows = ndim == 3 && kb == 1;
-                Band b{(int)k, x0, w, y0s[j], hs[j], nm, step_cost(ndim, w, hs[j], full_rows)};
+                const bool full_rows = kb == 1;
+                const int rows = sweep_rows_per_stage(ndim, f32, w, g.px, x0);
+                Band b{(int)k, x0, w, y0s[j], hs[j], nm, step_cost(ndim, w, hs[j], full_rows, rows)};
                 bands.push_back(b);
                 total += seg_cost(b, nm);
                 biggest = std::max(biggest, b.step * 4.0);

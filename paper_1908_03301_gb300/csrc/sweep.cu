@@ -49,8 +49,10 @@ struct SW {
     static constexpr int HH = NDIM == 3 ? 1 : 0;    // halo rows above/below a patch
     static constexpr int NARR = NDIM == 3 ? 7 : 6;  // r q p y gx gy [gz]
     static constexpr int WMAX = NDIM == 3 ? 1024 / (int)sizeof(T) : NC * VT;
-    static constexpr int SLOT = NDIM == 3 ? 7296 : ((NC * VT + 2 * V) * (int)sizeof(T) + 127) / 128 * 128;
-    static constexpr int S = NDIM == 3 ? 3 : 7;     // stages
+    // 2D: a slot holds one array's rows of a stage (up to two rows of the
+    // widest block, more rows of narrower whole-row blocks)
+    static constexpr int SLOT = NDIM == 3 ? 7296 : ((2 * NC * VT + 2 * V) * (int)sizeof(T) + 127) / 128 * 128;
+    static constexpr int S = NDIM == 3 ? 3 : 4;     // stages
     static constexpr int BAR = 128;
     static constexpr int STAGE = NARR * SLOT;
     static constexpr int RING = NDIM == 3 ? 4 * SLOT : 0;  // 2D keeps p rows in registers
@@ -60,6 +62,19 @@ struct SW {
 };
 
 enum { A_R = 0, A_Q = 1, A_P = 2, A_Y = 3, A_GX = 4, A_GY = 5, A_GZ = 6 };
+
+// Rows of a 2D segment staged together.  A block spanning whole padded rows
+// (x0 = 0, w = px) is contiguous in memory, so each array's rows of a stage
+// are one bulk copy; other blocks copy row by row.  Fewer, larger copies: the
+// copy engine spends a fixed time per copy (about 0.1 us on GB300).
+constexpr int RMAX2 = 16;
+template <typename T>
+__host__ __device__ __forceinline__ int rows_per_stage_2d(int w, int px, bool fullrow) {
+    using C = SW<T, 2>;
+    constexpr int cap = C::SLOT / (int)sizeof(T);
+    int R = fullrow ? (cap - 2 * C::V) / px : cap / (w + 2 * C::V);
+    return R < 1 ? 1 : (R > RMAX2 ? RMAX2 : R);
+}
 
 template <typename T>
 __device__ __forceinline__ T rnew(T r, T q, T a) { return fma(-a, q, r); }
@@ -211,6 +226,88 @@ __device__ __forceinline__ void produce_step(unsigned char *smem, uint64_t *full
     }
 }
 
+// Producer, 2D: the stage of march steps t0 .. t0+tn-1 (tn <= R rows).  Step
+// t finishes row me = m0+t+1 (r, q, p; y when owned) and applies the stencil
+// on row mt = m0+t (gx from t >= 0, gy from t >= -1).  Row j of a stage sits
+// at j * pitch in each slot.
+template <typename T>
+__device__ __forceinline__ void produce_stage_2d(unsigned char *smem, uint64_t *full, int b,
+                                                 const ProdSeg<T> &ps, int t0, int tn, bool fullrow,
+                                                 int lane) {
+    using C = SW<T, 2>;
+    constexpr int V = C::V;
+    const int w = ps.w, px = ps.px, nm = ps.nm;
+    const int me_lo = ps.m0 + t0 + 1, mt_lo = ps.m0 + t0;
+    const int jL0 = max(0, -me_lo), jL1 = min(tn, nm - me_lo);
+    const int jY0 = ps.first ? 0 : max(jL0, ps.m0 - me_lo), jY1 = ps.first ? 0 : min(jL1, ps.m1 - me_lo);
+    const int jX0 = max(max(0, -t0), -mt_lo), jX1 = min(tn, nm - mt_lo);
+    const int jG0 = max(max(0, -1 - t0), -mt_lo), jG1 = jX1;
+    const int nL = ps.first ? 1 : 3;
+    const int rL = max(0, jL1 - jL0), rY = max(0, jY1 - jY0), rX = max(0, jX1 - jX0), rG = max(0, jG1 - jG0);
+    const long long ms = ps.ms;
+    if (fullrow) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)sizeof(T) *
+                ((rL ? (uint32_t)nL * (uint32_t)(rL * px + 2 * V) : 0u) + (uint32_t)(rY * px) +
+                 (rX ? (uint32_t)(rX * px + V) : 0u) + (uint32_t)(rG * px));
+            mbar_arrive_expect_tx(&full[b], bytes);
+        }
+        __syncwarp();
+        if (lane < nL && rL) {
+            const T *src = lane == 0 ? ps.r : (lane == 1 ? ps.q : ps.p);
+            bulk_load(stage_arr<T, 2>(smem, b, lane) + jL0 * px, src + (long long)(me_lo + jL0) * ms,
+                      (uint32_t)(rL * px + 2 * V) * sizeof(T), &full[b]);
+        } else if (lane == 4 && rY) {
+            bulk_load(stage_arr<T, 2>(smem, b, A_Y) + jY0 * px, ps.y + (long long)(me_lo + jY0) * ms,
+                      (uint32_t)(rY * px) * sizeof(T), &full[b]);
+        } else if (lane == 5 && rX) {
+            bulk_load(stage_arr<T, 2>(smem, b, A_GX) + jX0 * px, ps.gx + (long long)(mt_lo + jX0) * ms,
+                      (uint32_t)(rX * px + V) * sizeof(T), &full[b]);
+        } else if (lane == 6 && rG) {
+            bulk_load(stage_arr<T, 2>(smem, b, A_GY) + jG0 * px, ps.gy + (long long)(mt_lo + jG0) * ms,
+                      (uint32_t)(rG * px) * sizeof(T), &full[b]);
+        }
+        return;
+    }
+    // row by row: pitches w + 2V (r q p), w (y, gy), w + V (gx)
+    if (lane == 0) {
+        const uint32_t bytes = (uint32_t)sizeof(T) *
+            ((uint32_t)(nL * rL) * (uint32_t)(w + 2 * V) + (uint32_t)(rY * w) + (uint32_t)(rX * (w + V)) +
+             (uint32_t)(rG * w));
+        mbar_arrive_expect_tx(&full[b], bytes);
+    }
+    __syncwarp();
+    const int total = nL * rL + rY + rX + rG;
+    for (int k = lane; k < total; k += 32) {
+        int kk = k;
+        if (kk < nL * rL) {
+            const int a = kk / rL, j = jL0 + kk % rL;
+            const T *src = a == 0 ? ps.r : (a == 1 ? ps.q : ps.p);
+            bulk_load(stage_arr<T, 2>(smem, b, a) + j * (w + 2 * V), src + (long long)(me_lo + j) * ms,
+                      (uint32_t)(w + 2 * V) * sizeof(T), &full[b]);
+            continue;
+        }
+        kk -= nL * rL;
+        if (kk < rY) {
+            const int j = jY0 + kk;
+            bulk_load(stage_arr<T, 2>(smem, b, A_Y) + j * w, ps.y + (long long)(me_lo + j) * ms,
+                      (uint32_t)w * sizeof(T), &full[b]);
+            continue;
+        }
+        kk -= rY;
+        if (kk < rX) {
+            const int j = jX0 + kk;
+            bulk_load(stage_arr<T, 2>(smem, b, A_GX) + j * (w + V), ps.gx + (long long)(mt_lo + j) * ms,
+                      (uint32_t)(w + V) * sizeof(T), &full[b]);
+            continue;
+        }
+        kk -= rX;
+        const int j = jG0 + kk;
+        bulk_load(stage_arr<T, 2>(smem, b, A_GY) + j * w, ps.gy + (long long)(mt_lo + j) * ms,
+                  (uint32_t)w * sizeof(T), &full[b]);
+    }
+}
+
 template <typename T, int NDIM>
 __device__ SegView seg_view(const SweepSeg &sg, const SweepInst &I) {
     using C = SW<T, NDIM>;
@@ -261,16 +358,24 @@ __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t
     pm1.zero(); p0.zero(); r_cur.zero(); r_next.zero(); mdown.zero();
     T h0l = T(0), h0r = T(0);  // p at row m, columns cx-1 and cx+VT (edge lanes)
     T a_pq = T(0), a_rq = T(0), a_qq = T(0), a_rr = T(0);
-    for (int t = -2; t < m1 - m0; t++, G++) {
-        const int b = (int)(G % S);
-        if (!mbar_wait_bounded(&full[b], (uint32_t)(G / S) & 1u, lim)) {
-            *s_err = 1;
-            lim = WAIT_LIMIT_AFTER_ERROR;
-        }
+    // stages of R rows; row j of a stage at j * pitch in each slot
+    const bool fullrow = x0 == 0 && w == px;
+    const int R = rows_per_stage_2d<T>(w, px, fullrow);
+    const int PL = fullrow ? px : w + 2 * V, PY = fullrow ? px : w, PGX = fullrow ? px : w + V;
+    const int L = m1 - m0;
+    for (int t0 = -2; t0 < L; t0 += R, G++) {
+      const int b = (int)(G % S);
+      if (!mbar_wait_bounded(&full[b], (uint32_t)(G / S) & 1u, lim)) {
+          *s_err = 1;
+          lim = WAIT_LIMIT_AFTER_ERROR;
+      }
+      const int tn = min(R, L - t0);
+      for (int j = 0; j < tn; j++) {
+        const int t = t0 + j;
         const int me = m0 + t + 1;
-        const T *sr = stage_arr<T, 2>(smem, b, A_R) + V + cx;
-        const T *sq = stage_arr<T, 2>(smem, b, A_Q) + V + cx;
-        const T *sp = stage_arr<T, 2>(smem, b, A_P) + V + cx;
+        const T *sr = stage_arr<T, 2>(smem, b, A_R) + j * PL + V + cx;
+        const T *sq = stage_arr<T, 2>(smem, b, A_Q) + j * PL + V + cx;
+        const T *sp = stage_arr<T, 2>(smem, b, A_P) + j * PL + V + cx;
         // ---- finish iteration k-1 on row me (registers) ----
         V8<T> pn;
         pn.zero();
@@ -302,7 +407,7 @@ __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t
                     } else {
                         V8<T> pv;
                         pv.ld(sp);
-                        yn.ld(stage_arr<T, 2>(smem, b, A_Y) + cx);
+                        yn.ld(stage_arr<T, 2>(smem, b, A_Y) + j * PY + cx);
 #pragma unroll
                         for (int k = 0; k < VT; k++) yn.v[k] = fma(alpha, pv.v[k], yn.v[k]);
                     }
@@ -319,10 +424,10 @@ __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t
             V8<T> gx, mup, qv;
             gx.zero();
             mup.zero();
-            const T *sgx = stage_arr<T, 2>(smem, b, A_GX) + V + cx;
+            const T *sgx = stage_arr<T, 2>(smem, b, A_GX) + j * PGX + V + cx;
             if (act) {
                 gx.ld(sgx);
-                mup.ld(stage_arr<T, 2>(smem, b, A_GY) + cx);
+                mup.ld(stage_arr<T, 2>(smem, b, A_GY) + j * PY + cx);
             }
             T left = __shfl_up_sync(0xffffffffu, p0.v[VT - 1], 1);
             T right = __shfl_down_sync(0xffffffffu, p0.v[0], 1);
@@ -353,15 +458,16 @@ __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t
             }
             mdown = mup;
         } else if (t == -1) {
-            if (act && m0 - 1 >= 0) mdown.ld(stage_arr<T, 2>(smem, b, A_GY) + cx);
+            if (act && m0 - 1 >= 0) mdown.ld(stage_arr<T, 2>(smem, b, A_GY) + j * PY + cx);
         }
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[b])) : "memory");
         pm1 = p0;
         p0 = pn;
         h0l = h1l;
         h0r = h1r;
         r_cur = r_next;
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[b])) : "memory");
     }
     acc[0] = (double)a_pq;
     acc[1] = (double)a_rq;
@@ -423,7 +529,10 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
             ps.px = g.px;
             ps.full = NDIM == 3 && sv.x0 == 0 && sv.w == g.px;
             ps.first = sv.first;
-            for (int t = -2; t < sv.m1 - sv.m0; t++, G++) {
+            const bool fullrow = sv.x0 == 0 && sv.w == g.px;
+            const int R = NDIM == 2 ? rows_per_stage_2d<T>(sv.w, g.px, fullrow) : 1;
+            const int L = sv.m1 - sv.m0;
+            for (int t = -2; t < L; t += R, G++) {
                 const int b = (int)(G % S);
                 if (G >= S) {
                     bool ok = true;
@@ -432,7 +541,10 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
                     if (!ok) lim = WAIT_LIMIT_AFTER_ERROR;
                     fence_proxy_async_smem();
                 }
-                produce_step<T, NDIM>(smem, full, b, ps, t, lane);
+                if constexpr (NDIM == 2)
+                    produce_stage_2d<T>(smem, full, b, ps, t, min(R, L - t), fullrow, lane);
+                else
+                    produce_step<T, NDIM>(smem, full, b, ps, t, lane);
             }
         }
         return;
@@ -711,6 +823,11 @@ int sweep_max_width(int ndim, int f32) {
     return f32 ? SW<float, 3>::WMAX : SW<double, 3>::WMAX;
 }
 int sweep_vt(int f32) { return f32 ? 2 : 1; }
+int sweep_rows_per_stage(int ndim, int f32, int w, int px, int x0) {
+    if (ndim != 2) return 1;
+    const bool fullrow = x0 == 0 && w == px;
+    return f32 ? rows_per_stage_2d<float>(w, px, fullrow) : rows_per_stage_2d<double>(w, px, fullrow);
+}
 bool sweep_patch_fits(int f32, int w, int h) {
     const long long es = f32 ? 4 : 8, V = 16 / es;
     const long long need = (long long)(h + 2) * (w + 2 * V) * es;

@@ -54,7 +54,22 @@ def run_plan(exe, ndim, f32, nsm, shape, dims_list):
     return grid, segs, nseg, cap, wmax
 
 
-def check_plan(plan, ndim, dims_list, f32=1, slack=1.30):
+def step_cost(ndim, f32, w, h, px, x0):
+    """The planner's cost of one march step: its nodes plus 100 node-equivalents
+    per bulk copy.  2D stages hold several rows (one copy per array over whole
+    rows, one per row otherwise): a slot holds 2080 floats / 1040 doubles."""
+    full = x0 == 0 and w == px
+    if ndim == 2:
+        cap, V = (2080, 4) if f32 else (1040, 2)
+        R = (cap - 2 * V) // px if full else cap // (w + 2 * V)
+        R = max(1, min(16, R))
+        copies = 6 / R if full else 6
+    else:
+        copies = 7 if full else 3 * (h + 2) + 4 * h + 1
+    return w * h + 100 * copies
+
+
+def check_plan(plan, ndim, dims_list, f32=1):
     grid, segs, nseg, cap, wmax = plan
     cover = []
     for d in dims_list:
@@ -76,8 +91,7 @@ def check_plan(plan, ndim, dims_list, f32=1, slack=1.30):
             cover[inst][0, m0:m1, x0:x0 + w] += 1
         assert slot not in slots[inst]
         slots[inst].add(slot)
-        copies = 6 if ndim == 2 else (7 if w == (dims_list[inst][0] + 3) // 4 * 4 else 3 * (h + 2) + 4 * h + 1)
-        load[cta] += (w * h + 100 * copies) * (m1 - m0 + 2)
+        load[cta] += step_cost(ndim, f32, w, h, (dims_list[inst][0] + 3) // 4 * 4, x0) * (m1 - m0 + 2)
     for k, c in enumerate(cover):
         assert (c == 1).all(), f"network {k}: nodes covered {c.min()}..{c.max()} times"
         assert slots[k] == set(range(nseg[k]))
