@@ -43,9 +43,13 @@ def args_():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="fbm2048", choices=["fbm2048", "perc3d", "batch", "serve"],
+    ap.add_argument("--workload", default="fbm2048",
+                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso"],
                     help="fbm2048: the headline 2048^2 solve; perc3d: 256^3 percolation; batch: "
-                         "512 networks in one batched solve; serve: the request queue")
+                         "512 networks in one batched solve; serve: the request queue; aniso: "
+                         "K_x/K_y of anisotropic FBM networks (both axes batched)")
+    ap.add_argument("--aniso-size", type=int, default=512)
+    ap.add_argument("--aniso-real", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -560,6 +564,48 @@ def run_serve(a):
     print(json.dumps(line), flush=True)
 
 
+def run_aniso(a):
+    """Permeability anisotropy K_x/K_y (Sec. VI.B, Fig. 10): for H in {0.75,
+    0.35} and beta_x/beta_y in {0.2, 0.5, 1, 2, 5}, --aniso-real realizations
+    of an n x n anisotropic FBM network (Eq. 2, sigma = 1), each solved along x
+    and along y; every (H, ratio) is one net_solve_batch of 2 x realizations.
+    Reports min / median / max of K_x/K_y per cell and solves/s overall."""
+    import numpy as np
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    n, R = a.aniso_size, a.aniso_real
+    cells, total_s, solves, worst = [], 0.0, 0, 0.0
+    for hi, H in enumerate(netgen.ANISO_H):
+        for ri, ratio in enumerate(netgen.ANISO_RATIOS):
+            specs = [netgen.aniso_instance(hi, ri, r, n=n) for r in range(R)]
+            nets = [ns.Network(d, p, flow_axis=ax) for d, p in specs for ax in (0, 1)]
+            t = time.perf_counter()
+            res = ns.solve_batch(nets, ns.make_opts(tol_rel=TOL_REL))
+            total_s += time.perf_counter() - t
+            for net in nets:
+                net.close()
+            solves += len(res)
+            assert all(x.status == 0 for x in res), [x.status for x in res]
+            kx = np.array([res[2 * r].k_eff for r in range(R)])
+            ky = np.array([res[2 * r + 1].k_eff for r in range(R)])
+            worst = max(worst, max(x.g_eff_err for x in res))
+            ratio_k = kx / ky
+            cells.append({"H": H, "beta_x_over_beta_y": ratio, "kx_over_ky_min": float(ratio_k.min()),
+                          "kx_over_ky_median": float(np.median(ratio_k)),
+                          "kx_over_ky_max": float(ratio_k.max())})
+    line = {"metric": METRIC, "workload": "aniso", "value": solves / total_s, "unit": "solves/s",
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{n}x{n} anisotropic FBM networks (Eq. 2), sigma=1, {R} realizations "
+                                   "per (H, beta_x/beta_y), K_x and K_y batched", "tol_rel": TOL_REL},
+            "solves": solves, "seconds": total_s, "max_geff_err_estimate": worst, "cells": cells,
+            "paper_ranges": {"H=0.75": [0.6, 1.6], "H=0.35": [0.5, 2.5],
+                             "note": "Fig. 10 bounds (3.6M-node networks); context only"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.profile_solve:
@@ -568,9 +614,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if a.workload in ("perc3d", "serve") and a.impl == "ours":
+    if a.workload in ("perc3d", "serve", "aniso") and a.impl == "ours":
         if rank == 0:
-            {"perc3d": run_perc3d, "serve": run_serve}[a.workload](a)
+            {"perc3d": run_perc3d, "serve": run_serve, "aniso": run_aniso}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)

@@ -120,6 +120,33 @@ def fbm_field(shape, hurst, gen):
     return field
 
 
+def fbm_field_aniso(shape, hurst, beta_x, beta_y, gen):
+    """2D FBM with the anisotropic spectral density of Eq. 2,
+    S(w) ~ (beta_x w_x^2 + beta_y w_y^2)^-(H+1), by the same spectral
+    filtering as fbm_field (which it equals for beta_x = beta_y = 1).
+    shape = (ny, nx).  beta_x / beta_y > 1 gives layers parallel to x."""
+    ny, nx = shape
+    wy = np.fft.fftfreq(ny)[:, None]
+    wx = np.fft.fftfreq(nx)[None, :]
+    k2 = beta_x * wx * wx + beta_y * wy * wy
+    k2[0, 0] = 1.0
+    amp = k2 ** (-(hurst + 1.0) / 2.0)
+    amp[0, 0] = 0.0
+    noise = gen.standard_normal(shape) + 1j * gen.standard_normal(shape)
+    field = np.fft.ifftn(noise * amp).real
+    field -= field.mean()
+    sd = field.std()
+    if sd > 0:
+        field /= sd
+    return field
+
+
+def fbm_aniso_bonds(dims, hurst, beta_x, beta_y, sigma, gen):
+    """Anisotropic correlated conductances g = exp(sigma * B_b), B from Eq. 2."""
+    B = fbm_field_aniso(node_shape(dims), hurst, beta_x, beta_y, gen)
+    return [np.exp(sigma * b) for b in _node_to_bonds(B, dims)]
+
+
 def fbm_bonds(dims, hurst, sigma, gen):
     """Correlated conductances g = exp(sigma * B_b), B an FBM on the nodes."""
     B = fbm_field(node_shape(dims), hurst, gen)
@@ -147,6 +174,23 @@ def fbm_stratified_bonds(dims, hurst, sigma, gen, noise=0.1):
 def percolate(planes, p, gen):
     """Bond percolation: keep each bond open with probability p (independent)."""
     return [np.where(gen.random(g.shape) < p, g, 0.0).astype(g.dtype) for g in planes]
+
+
+def percolate_sorted(planes, q):
+    """Correlated percolation (Sec. VI.B): close the fraction q of all bonds
+    with the smallest conductances, so that the closed bonds keep the field's
+    correlations.  Ties are broken by position (plane, then index)."""
+    flat = np.concatenate([g.ravel() for g in planes])
+    k = int(np.floor(q * flat.size))
+    closed = np.zeros(flat.size, bool)
+    if k > 0:
+        closed[np.argsort(flat, kind="stable")[:k]] = True
+    out, o = [], 0
+    for g in planes:
+        c = closed[o:o + g.size].reshape(g.shape)
+        out.append(np.where(c, 0.0, g).astype(g.dtype))
+        o += g.size
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -201,6 +245,20 @@ def batch_instance(i, smin=64, smax=1024, p=0.55, sigma=1.0):
     if i % 2 == 0:
         planes = percolate(planes, p, gen)
     return dims, planes
+
+
+def aniso_instance(h_index, ratio_index, r, n=512, sigma=1.0):
+    """Realization r of the permeability-anisotropy workload (Sec. VI.B,
+    Fig. 10): an n x n network with conductances exp(sigma * B), B an
+    anisotropic FBM (Eq. 2) with H = ANISO_H[h_index] and
+    beta_x / beta_y = ANISO_RATIOS[ratio_index] (beta_y = 1)."""
+    gen = rng(SEED_BASE + 1000 * 5 + 100 * (len(ANISO_RATIOS) * h_index + ratio_index) + r)
+    dims = (n, n)
+    return dims, fbm_aniso_bonds(dims, ANISO_H[h_index], ANISO_RATIOS[ratio_index], 1.0, sigma, gen)
+
+
+ANISO_H = (0.75, 0.35)
+ANISO_RATIOS = (0.2, 0.5, 1.0, 2.0, 5.0)
 
 
 def batch_instance_dims(i, smin=64, smax=1024):

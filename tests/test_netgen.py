@@ -1,0 +1,48 @@
+"""Input generators (no solver arithmetic): the anisotropic FBM of Eq. 2 and
+correlated (sorted-removal) percolation of Sec. VI.B."""
+import numpy as np
+
+from paper_1908_03301_gb300 import netgen
+
+
+def test_aniso_fbm_reduces_to_isotropic_for_equal_betas():
+    a = netgen.fbm_field((64, 48), 0.7, netgen.rng(3))
+    b = netgen.fbm_field_aniso((64, 48), 0.7, 1.0, 1.0, netgen.rng(3))
+    assert np.array_equal(a, b)
+
+
+def test_aniso_fbm_is_smoother_along_the_heavier_beta():
+    """beta_x / beta_y > 1 damps the x frequencies: layers parallel to x, so
+    increments along x are smaller than along y (and the reverse for < 1)."""
+    for ratio, along_x_smaller in ((5.0, True), (0.2, False)):
+        dx, dy = [], []
+        for r in range(4):
+            f = netgen.fbm_field_aniso((256, 256), 0.35, ratio, 1.0, netgen.rng(100 + r))
+            dx.append(np.mean(np.diff(f, axis=1) ** 2))
+            dy.append(np.mean(np.diff(f, axis=0) ** 2))
+        assert (np.mean(dx) < np.mean(dy)) == along_x_smaller
+
+
+def test_aniso_field_is_normalised():
+    f = netgen.fbm_field_aniso((128, 96), 0.75, 2.0, 1.0, netgen.rng(7))
+    assert abs(f.mean()) < 1e-12 and abs(f.std() - 1.0) < 1e-12
+
+
+def test_sorted_removal_closes_the_smallest_fraction():
+    dims, planes = netgen.aniso_instance(1, 2, 0, n=96)
+    for q in (0.0, 0.3, 0.5):
+        out = netgen.percolate_sorted(planes, q)
+        flat_in = np.concatenate([g.ravel() for g in planes])
+        flat = np.concatenate([g.ravel() for g in out])
+        closed = flat == 0.0
+        assert closed.sum() == int(np.floor(q * flat.size))
+        if closed.any():
+            assert flat_in[closed].max() <= flat_in[~closed].min()
+        assert np.array_equal(flat[~closed], flat_in[~closed])
+
+
+def test_aniso_instances_are_seeded_and_distinct():
+    d1, p1 = netgen.aniso_instance(0, 1, 2, n=64)
+    d2, p2 = netgen.aniso_instance(0, 1, 2, n=64)
+    d3, p3 = netgen.aniso_instance(0, 1, 3, n=64)
+    assert d1 == (64, 64) and np.array_equal(p1[0], p2[0]) and not np.array_equal(p1[0], p3[0])
