@@ -211,6 +211,60 @@ int or_labels(const or_desc *d, const double *const g[3], int32_t *label, uint8_
     return 0;
 }
 
+/*
+ * Backbone of the spanning clusters: the nodes that remain when dead-end
+ * trees are stripped.  A spanning interior node with at most one open bond
+ * to nodes still present (face nodes always count as present) carries no
+ * current: its only bond has no flow, so its pressure is that of its single
+ * neighbour.  Removing such nodes one at a time until none is left gives a
+ * unique set (the part of each spanning cluster in which every interior node
+ * keeps at least two links, the two faces never removed).  This follows that
+ * definition directly with a work list of removable nodes.
+ * backbone[i] = 1 for spanning nodes that remain, 0 for every other node.
+ * Returns 0, or -1 on bad input.
+ */
+int or_backbone(const or_desc *d, const double *const g[3], uint8_t *backbone) {
+    if (validate(d, g)) return -1;
+    const int64_t N = n_nodes(d);
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    uint8_t *cls = (uint8_t *)malloc((size_t)N);
+    int32_t *deg = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    int64_t *work = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int rc = -1;
+    if (!label || !cls || !deg || !work) goto out;
+    if (or_labels(d, g, label, cls)) goto out;
+    int64_t c[3], j, top = 0;
+    double gij;
+    /* present = spanning interior nodes and all face nodes */
+    for (int64_t i = 0; i < N; i++) backbone[i] = cls[i] == CLS_SPANNING;
+    for (int64_t i = 0; i < N; i++) {
+        if (!backbone[i]) continue;
+        coords(d, i, c);
+        for (int k = 0; k < 2 * d->ndim; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij) || !(gij > 0.0)) continue;
+            if (backbone[j] || cls[j] == CLS_FACE_IN || cls[j] == CLS_FACE_OUT) deg[i]++;
+        }
+        if (deg[i] <= 1) work[top++] = i;
+    }
+    while (top > 0) {
+        const int64_t i = work[--top];
+        if (!backbone[i]) continue;
+        backbone[i] = 0;
+        coords(d, i, c);
+        for (int k = 0; k < 2 * d->ndim; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij) || !(gij > 0.0) || !backbone[j]) continue;
+            if (--deg[j] == 1) work[top++] = j;  /* reaches 1 once: pushed once */
+        }
+    }
+    rc = 0;
+out:
+    free(label);
+    free(cls);
+    free(deg);
+    free(work);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* vector helpers (fixed-order sums)                                   */
 /* ------------------------------------------------------------------ */

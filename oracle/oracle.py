@@ -74,6 +74,8 @@ def _load():
         dp3 = C.POINTER(C.c_double) * 3
         lib.or_labels.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p, C.c_void_p]
         lib.or_labels.restype = C.c_int
+        lib.or_backbone.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p]
+        lib.or_backbone.restype = C.c_int
         lib.or_residual.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p, C.c_void_p]
         lib.or_residual.restype = C.c_int
         lib.or_solve.argtypes = [C.POINTER(_Desc), dp3, C.c_double, C.c_int64, C.c_int,
@@ -113,6 +115,17 @@ def labels(dims, planes, flow_axis=0):
     if lib.or_labels(C.byref(desc), ptrs, lab.ctypes.data, cls.ctypes.data) != 0:
         raise ValueError("invalid network")
     return lab.reshape(shape), cls.reshape(shape)
+
+
+def backbone(dims, planes, flow_axis=0):
+    """Spanning-cluster nodes left after stripping dead-end trees (bool,
+    node-shaped); every other node is False."""
+    lib = _load()
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    out = np.empty(N, np.uint8)
+    if lib.or_backbone(C.byref(desc), ptrs, out.ctypes.data) != 0:
+        raise ValueError("invalid network")
+    return out.reshape(shape).astype(bool)
 
 
 def residual(dims, planes, P, flow_axis=0):

@@ -245,3 +245,107 @@ def test_invalid_inputs_rejected():
         oracle.solve(dims, bad)
     with pytest.raises(ValueError):
         oracle.solve((2, 8), netgen.uniform((2, 8)))
+
+
+# ---------------------------------------------------------------- backbone (dead-end stripping)
+def _nx_backbone(dims, planes, flow_axis=0):
+    """Backbone by networkx's k-core: the graph of open bonds among the
+    spanning nodes and the face nodes (face-face bonds left out), every face
+    node tied to a triangle so that it never drops below degree 2 while it
+    keeps one interior link.  The 2-core's interior nodes are the backbone."""
+    nx = pytest.importorskip("networkx")
+    lab, cls = oracle.labels(dims, planes, flow_axis)
+    cls = cls.reshape(-1)
+    N = int(np.prod(dims))
+    ndim = len(dims)
+    ext = list(dims) + [1] * (3 - ndim)
+    face = (cls == oracle.CLS_FACE_IN) | (cls == oracle.CLS_FACE_OUT)
+    keep = (cls == oracle.CLS_SPANNING) | face
+    G = nx.Graph()
+    G.add_nodes_from(np.where(keep)[0].tolist())
+    for d in range(ndim):
+        g = planes[d].reshape(-1)
+        n = list(ext)
+        n[d] -= 1
+        idx = np.arange(int(np.prod(n)))
+        c = [idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1])]
+        i = c[0] + ext[0] * (c[1] + ext[1] * c[2])
+        step = [1, ext[0], ext[0] * ext[1]][d]
+        j = i + step
+        ok = (g > 0) & keep[i] & keep[j] & ~(face[i] & face[j])
+        G.add_edges_from(zip(i[ok].tolist(), j[ok].tolist()))
+    G.add_edges_from([("S", "A"), ("A", "B"), ("B", "S")])
+    G.add_edges_from(("S", int(f)) for f in np.where(face)[0])
+    core = nx.k_core(G, 2)
+    out = np.zeros(N, bool)
+    for v in core.nodes:
+        if not isinstance(v, str) and cls[v] == oracle.CLS_SPANNING:
+            out[v] = True
+    return out
+
+
+@pytest.mark.parametrize("dims,f,p,seed", [((14, 11), 0, 0.62, 1), ((12, 15), 1, 0.58, 2),
+                                           ((9, 8, 7), 0, 0.36, 3), ((8, 9, 10), 2, 0.33, 4),
+                                           ((30, 30), 0, 0.55, 5), ((16, 16, 16), 1, 0.3, 6)])
+def test_backbone_equals_kcore(dims, f, p, seed):
+    gen = netgen.rng(9100 + seed)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), p, gen)
+    bb = oracle.backbone(dims, planes, f).reshape(-1)
+    np.testing.assert_array_equal(bb, _nx_backbone(dims, planes, f))
+
+
+def test_backbone_hand_made_tree_on_a_path():
+    """A single open path along row 2 of a 7x5 network plus a branch of three
+    bonds hanging from it (a dead end) and a loop of four bonds beside it: the
+    backbone is the path and the loop, the branch is stripped."""
+    dims = (7, 5)
+    gx = np.zeros((5, 6))
+    gy = np.zeros((4, 7))
+    gx[2, :] = 1.0           # the path x = 0..6 on row 2
+    gy[2, 3] = 2.0           # branch (3,2)-(3,3)
+    gx[3, 3] = 2.0           # (3,3)-(4,3)
+    gy[3, 4] = 2.0           # (4,3)-(4,4)
+    gy[0, 2] = gy[1, 2] = 3.0  # loop (2,0)-(2,1)-(2,2) ...
+    gx[0, 2] = 3.0             # ... (2,0)-(3,0)
+    gy[0, 3] = gy[1, 3] = 3.0  # (3,0)-(3,1)-(3,2)
+    bb = oracle.backbone(dims, [gx, gy])
+    want = np.zeros((5, 7), bool)
+    want[2, 1:6] = True
+    want[0, 2] = want[1, 2] = want[0, 3] = want[1, 3] = True
+    np.testing.assert_array_equal(bb, want)
+
+
+def test_backbone_stripping_is_exact():
+    """Closing every bond that touches a stripped node leaves G unchanged, and
+    each stripped node's pressure equals that of a backbone or face neighbour
+    reached through stripped nodes only (no current flows into a dead end)."""
+    gen = netgen.rng(9200)
+    dims = (22, 20, 18)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.34, gen)
+    full = oracle.solve(dims, planes, tol=1e-14)
+    bb = oracle.backbone(dims, planes)
+    span = full.cls == oracle.CLS_SPANNING
+    dead = span & ~bb
+    assert dead.any() and bb.any()
+    cut = []
+    for d in range(3):
+        ax = 2 - d
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        g = planes[d].copy()
+        g[dead[tuple(lo)] | dead[tuple(hi)]] = 0.0
+        cut.append(g)
+    red = oracle.solve(dims, cut, tol=1e-14)
+    assert rel(red.g_eff, full.g_eff) < 1e-10
+    # across every open bond that touches a stripped node there is no drop
+    for d in range(3):
+        ax = 2 - d
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        touch = (planes[d] > 0) & (dead[tuple(lo)] | dead[tuple(hi)])
+        drop = np.abs(full.P[tuple(lo)] - full.P[tuple(hi)])[touch]
+        assert drop.max() < 1e-9
