@@ -371,7 +371,7 @@ def run_profile_solve(a):
     net.close()
     torch.cuda.synchronize()
     print(json.dumps({"profile_solve": True, "dims": list(dims), "inner_iters": r.inner_iters,
-                      "inner_ms": r.inner_ms, "n_active": r.n_active,
+                      "inner_ms": r.inner_ms, "n_active": r.n_active, "n_solved": r.n_solved,
                       "inner_launches": r.inner_launches}), flush=True)
 
 
@@ -418,7 +418,7 @@ def run_perc3d(a):
     ms64, res64 = steps(ns.NET_FP64, max(1, a.fp64_steps), 1)
     r0 = res[-1]
     N = dims[0] * dims[1] * dims[2]
-    b_act = 44 * r0.n_active
+    b_act = 44 * r0.n_solved
     b_grid = 44 * N
     it_s = r0.inner_ms / 1e3 / max(1, r0.inner_iters)
     peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
@@ -429,7 +429,7 @@ def run_perc3d(a):
             "steps": len(ms), "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "3D 256^3 bond percolation p=0.26, FBM H=0.3 sigma=1, FP32 "
                                    "conductances", "nodes": N, "n_active": r0.n_active,
-                       "tol_rel": TOL_REL},
+                       "n_solved": r0.n_solved, "tol_rel": TOL_REL},
             "accuracy": {"g_eff": r0.g_eff, "g_eff_fp64": res64[-1].g_eff,
                          "rel_mixed_vs_fp64": abs(r0.g_eff - res64[-1].g_eff) / max(abs(res64[-1].g_eff), 1e-300),
                          "rel_err_vs_oracle": (abs(r0.g_eff - ref["g_eff"]) / ref["g_eff"]) if ref else None,
@@ -490,12 +490,14 @@ def run_batch(a, rank=0, world=1, local=0):
             torch.cuda.synchronize()
             times.append(replicas.max_over_ranks(time.perf_counter() - t, device=dev))
     clocks = clk.summary()
-    local_res = {i: (r.status, r.inner_iters * r.n_active, r.ms, r.fp64_fallback)
-                 for i, r in zip(mine, res)}
+    local_res = {i: (r.status, r.inner_iters * r.n_solved, r.ms, r.fp64_fallback,
+                     r.inner_iters * specs[k][0][0] * specs[k][0][1])
+                 for k, (i, r) in enumerate(zip(mine, res))}
     allr = replicas.gather_results(local_res, a.batch_count)
     if rank != 0:
         return
     ui = sum(x[1] for x in allr)
+    li = sum(x[4] for x in allr)
     ok = sum(x[0] == 0 for x in allr)
     lat = sorted(x[2] for x in allr)
     line = {"metric": METRIC, "workload": "batch", "value": a.batch_count * len(times) / sum(times),
@@ -508,6 +510,10 @@ def run_batch(a, rank=0, world=1, local=0):
                        "parallelism": f"networks sharded over {world} GPU(s), no collective"},
             "converged": ok, "unknown_iterations_per_s": ui / statistics.mean(times),
             "algorithmic_gbs": 40 * ui / statistics.mean(times) / 1e9,
+            "lattice_gbs": 40 * li / statistics.mean(times) / 1e9,
+            "bytes_note": "algorithmic = 40 B x unknowns in the linear system (dead ends and "
+                          "non-spanning clusters excluded) x CG iterations; lattice = 40 B x "
+                          "all lattice nodes x CG iterations (what the sweep streams)",
             "per_network_ms_p50": lat[len(lat) // 2], "per_network_ms_p99": lat[int(0.99 * (len(lat) - 1))],
             "fp64_fallbacks": sum(x[3] for x in allr), "clocks": clocks}
     print(json.dumps(line), flush=True)

@@ -146,7 +146,7 @@ typedef struct {
     double rel_residual;     /* ||b - G P||_2 / ||b||_2, FP64 true residual */
     double max_imbalance;    /* max nodal current imbalance |b - G P|_inf */
     double energy_g;         /* sum_bonds g dP_b^2 / (p_in - p_out)^2 */
-    int64_t n_active;        /* unknowns in spanning clusters */
+    int64_t n_active;        /* nodes of spanning clusters */
     int outer_iters;         /* refinement steps taken */
     int64_t inner_iters;     /* CG iterations summed over refinement steps */
     int fp64_fallback;       /* 1 if the inner solve was switched to FP64 */
@@ -155,6 +155,8 @@ typedef struct {
     int64_t inner_launches;  /* inner CG kernel launches (incl. no-op tails) */
     net_status status;
     double g_eff_err;        /* estimated relative error of g_eff (see tol_geff) */
+    int64_t n_solved;        /* unknowns of the linear system: n_active less the
+                                dead-end nodes (see net_get_backbone) */
 } net_result;
 
 /* Fill *opts with the defaults listed in net_opts. */
@@ -208,6 +210,24 @@ net_status net_get_pressure(net_t *net, double *dst, int64_t n, int dst_on_devic
  * nodes into host buffers of at least n entries.  Either pointer may be NULL.
  */
 net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int64_t n);
+
+/*
+ * Backbone of the spanning clusters: backbone[i] = 1 for the spanning nodes
+ * that remain once dead-end trees are stripped, 0 for every other node
+ * (host buffer of at least n >= N entries, node layout).
+ *
+ * A spanning node with at most one open bond to nodes still present (face
+ * nodes always count) carries no current: its one bond has no flow, so its
+ * pressure equals its neighbour's.  net_create removes such nodes in rounds
+ * until none is left (the result is unique); they keep their cluster label
+ * and class NET_CLS_SPANNING, but leave the linear system of Eq. 3: the
+ * diagonal and the CG sweeps cover the backbone only, and each removed node
+ * takes the pressure of the backbone or face node its tree hangs from before
+ * every residual pass.  This is exact (the paper solves the whole cluster;
+ * it says that near the percolation threshold much of it carries no flow).
+ * Set NETSOLVE_PRUNE=0 in the environment to keep the trees in the system.
+ */
+net_status net_get_backbone(net_t *net, uint8_t *backbone, int64_t n);
 
 /* Release the network's device state.  NULL is accepted. */
 net_status net_destroy(net_t *net);

@@ -121,6 +121,7 @@ void BatchEngine::finish(BatchItem *it, net_status st) {
     r.inner_iters = it->inner_total;
     r.fp64_fallback = it->fallback;
     r.g_eff_err = geff_err(n);
+    r.n_solved = n->n_solved;
     r.ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - it->t_start).count();
     r.status = st;
     if (st != NET_OK) it->err = last_error();

@@ -40,9 +40,11 @@ struct Geom {
 };
 
 // Cluster classes (same values as the NET_CLS_* constants of the C ABI).
+// CLS_DANGLING is internal: a node of a spanning cluster on a dead-end tree,
+// left out of the linear system (reported as CLS_SPANNING).
 enum : uint8_t {
     CLS_ISOLATED = 0, CLS_INLET = 1, CLS_OUTLET = 2, CLS_SPANNING = 3,
-    CLS_FACE_IN = 4, CLS_FACE_OUT = 5, CLS_GHOST = 255
+    CLS_FACE_IN = 4, CLS_FACE_OUT = 5, CLS_DANGLING = 6, CLS_GHOST = 255
 };
 
 // Scalars of one inner CG solve, in device memory.  The fused iteration
@@ -83,9 +85,12 @@ struct OuterScal {
 // Sums of the set-up pass.
 struct SetupScal {
     double bb;             // ||b||^2
-    unsigned long long n_active;
+    unsigned long long n_active;  // nodes of spanning clusters
+    unsigned long long n_solved;  // of them, unknowns of the linear system
     unsigned int counter;
     unsigned int bad;      // nonzero: a conductance was negative / NaN / inf
+    unsigned int pruned;   // dead-end nodes removed by the last pruning rounds
+    unsigned int pad_;
 };
 
 // ---------------------------------------------------------------------------

@@ -15,6 +15,19 @@ cudaError_t launch_pack_bonds(const Geom &g, int d, const void *src, int src_f32
 // Cluster labelling (union-find, min-index roots) and classes.
 cudaError_t launch_labels(const Geom &g, const void *const graw[3], int f32, int *parent,
                           unsigned int *flags, uint8_t *cls, cudaStream_t st);
+// Dead-end stripping (see kernels_setup.cu): one round over the lattice
+// (nodes removed in it get pr = round and their anchor; *count += removed),
+// then mark them CLS_DANGLING and resolve anchors to roots by `passes`
+// pointer-jumping passes (root aliases the anchor array).
+cudaError_t launch_prune_round(const Geom &g, const void *const graw[3], int f32, const uint8_t *cls,
+                               unsigned int *pr, int *anchor, unsigned int round, unsigned int *count,
+                               cudaStream_t st);
+cudaError_t launch_prune_finish(const Geom &g, uint8_t *cls, const unsigned int *pr, int *root,
+                                int passes, cudaStream_t st);
+// x at every dead-end node := x at its root (root[i] = -1 elsewhere).
+cudaError_t launch_fill_dangling(const Geom &g, const int *root, double *x, cudaStream_t st);
+// Compact uint8 mask of the backbone (spanning nodes left in the system).
+cudaError_t launch_backbone(const Geom &g, const uint8_t *cls, uint8_t *out, cudaStream_t st);
 // Diagonal scaling, initial pressures, ||b||^2 and the active count.
 cudaError_t launch_build_system(const Geom &g, const void *const graw[3], int f32,
                                 const uint8_t *cls, double *dis, double *x, SetupScal *ss,
@@ -103,6 +116,8 @@ struct OuterArgs {
     double bnorm;         // ||b||_2
     long long max_inner, stag_window;
     double *partials;
+    const int *root;      // dead-end nodes' roots (NULL: none); their x is
+                          // refreshed before the residual pass
 };
 int outer_grid_blocks(const Geom &g);
 cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st);

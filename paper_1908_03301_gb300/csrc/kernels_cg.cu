@@ -472,6 +472,11 @@ cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (a.root) {
+        // dead-end nodes take their root's pressure (no current in a dead end)
+        cudaError_t e = launch_fill_dangling(a.g, a.root, a.x, st);
+        if (e != cudaSuccess) return e;
+    }
     if (a.g.ndim == 2) {
         if (r32) return i32 ? launch_outer_t<float, float, 2>(a, st) : launch_outer_t<float, double, 2>(a, st);
         return i32 ? launch_outer_t<double, float, 2>(a, st) : launch_outer_t<double, double, 2>(a, st);

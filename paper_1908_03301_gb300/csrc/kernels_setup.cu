@@ -174,6 +174,101 @@ __global__ void lab_final(Geom g, const int *parent, const unsigned int *flags, 
     }
 }
 
+// ------------------------------------------------------------------ dead ends
+// One round of stripping dead-end trees from the spanning clusters: a
+// spanning node still present with at most one open bond to a present node
+// (face nodes are always present) carries no current; it is removed in this
+// round (pr = round) and remembers that neighbour (anchor) as the node whose
+// pressure it takes.  Nodes removed in the same round still count as present
+// for each other, so the result does not depend on thread order.
+__global__ void prune_round_kernel(Geom g, const void *g0, const void *g1, const void *g2, int f32,
+                                   const uint8_t *__restrict__ cls, unsigned int *pr, int *anchor,
+                                   unsigned int round, unsigned int *count) {
+    const long long n = grid_nodes(g);
+    const void *gp[3] = {g0, g1, g2};
+    unsigned int mine = 0;
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
+         t += (long long)gridDim.x * NT) {
+        int x, y, z;
+        unflatten(g, t, x, y, z);
+        const long long i = g.idx(x, y, z);
+        if (cls[i] != CLS_SPANNING || pr[i] != 0u) continue;
+        int links = 0;
+        long long last = -1;
+        for (int d = 0; d < g.ndim; d++) {
+            const long long s = g.stride(d);
+            for (int side = 0; side < 2; side++) {
+                const long long j = side ? i - s : i + s;
+                if (!(bond_at(gp[d], f32, side ? j : i) > 0.0)) continue;
+                const uint8_t cj = cls[j];
+                const unsigned int pj = *(volatile const unsigned int *)&pr[j];
+                if (cj == CLS_FACE_IN || cj == CLS_FACE_OUT || (cj == CLS_SPANNING && (pj == 0u || pj == round))) {
+                    links++;
+                    last = j;
+                }
+            }
+        }
+        if (links <= 1) {
+            pr[i] = round;
+            anchor[i] = (int)last;
+            mine++;
+        }
+    }
+    if (mine) atomicAdd(count, mine);
+}
+
+// Mark the removed nodes CLS_DANGLING.
+__global__ void prune_mark_kernel(Geom g, uint8_t *cls, const unsigned int *pr) {
+    const long long n = grid_nodes(g);
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
+         t += (long long)gridDim.x * NT) {
+        int x, y, z;
+        unflatten(g, t, x, y, z);
+        const long long i = g.idx(x, y, z);
+        if (pr[i] != 0u) cls[i] = CLS_DANGLING;
+    }
+}
+
+// Pointer jumping along the anchors: a removed node's anchor was present
+// when it was removed (removed later, or never), so following anchors ends
+// at a backbone or face node; each pass doubles the distance covered.
+__global__ void prune_jump_kernel(Geom g, const unsigned int *pr, int *root) {
+    const long long n = grid_nodes(g);
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
+         t += (long long)gridDim.x * NT) {
+        int x, y, z;
+        unflatten(g, t, x, y, z);
+        const long long i = g.idx(x, y, z);
+        if (pr[i] == 0u) continue;
+        const int a = root[i];
+        if (a >= 0 && pr[a] != 0u) root[i] = *(volatile const int *)&root[a];
+    }
+}
+
+// A dead-end node's pressure is that of the node its tree hangs from.
+__global__ void fill_dangling_kernel(Geom g, const int *__restrict__ root, double *x) {
+    const long long n = grid_nodes(g);
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
+         t += (long long)gridDim.x * NT) {
+        int cx, cy, cz;
+        unflatten(g, t, cx, cy, cz);
+        const long long i = g.idx(cx, cy, cz);
+        const int r = root[i];
+        if (r >= 0) x[i] = x[r];
+    }
+}
+
+__global__ void backbone_kernel(Geom g, const uint8_t *cls, uint8_t *out) {
+    const long long n = grid_nodes(g);
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
+         t += (long long)gridDim.x * NT) {
+        int cx, cy, cz;
+        unflatten(g, t, cx, cy, cz);
+        if (cx >= g.nx) continue;
+        out[cx + (long long)g.nx * (cy + (long long)g.ny * cz)] = cls[g.idx(cx, cy, cz)] == CLS_SPANNING;
+    }
+}
+
 // ------------------------------------------------------------------ system
 __global__ void build_system_kernel(Geom g, const void *g0, const void *g1, const void *g2,
                                     int f32, const uint8_t *__restrict__ cls,
@@ -183,7 +278,7 @@ __global__ void build_system_kernel(Geom g, const void *g0, const void *g1, cons
     const void *gp[3] = {g0, g1, g2};
     const long long sf = g.stride(g.f);
     const double dP = g.p_in - g.p_out;
-    double bb = 0.0, na = 0.0;
+    double bb = 0.0, na = 0.0, ns = 0.0;
     for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
          t += (long long)gridDim.x * NT) {
         int cx, cy, cz;
@@ -195,28 +290,36 @@ __global__ void build_system_kernel(Geom g, const void *g0, const void *g1, cons
         switch (c) {
         case CLS_FACE_IN: case CLS_INLET: xv = g.p_in; break;
         case CLS_FACE_OUT: case CLS_OUTLET: xv = g.p_out; break;
-        case CLS_SPANNING: xv = g.p_in - dP * (double)cf / (double)(g.nf - 1); break;
+        case CLS_SPANNING: case CLS_DANGLING: xv = g.p_in - dP * (double)cf / (double)(g.nf - 1); break;
         default: xv = 0.0;
         }
+        if (c == CLS_DANGLING) na += 1.0;
         if (c == CLS_SPANNING) {
+            // D_i over the bonds of the linear system: dead-end neighbours
+            // are not part of it
             double D = 0.0;
-            for (int d = 0; d < g.ndim; d++)
-                D += bond_at(gp[d], f32, i) + bond_at(gp[d], f32, i - g.stride(d));
+            for (int d = 0; d < g.ndim; d++) {
+                const long long s = g.stride(d);
+                if (cls[i + s] != CLS_DANGLING) D += bond_at(gp[d], f32, i);
+                if (cls[i - s] != CLS_DANGLING) D += bond_at(gp[d], f32, i - s);
+            }
             dv = 1.0 / sqrt(D);
             double b = 0.0;
             if (cf == 1) b += bond_at(gp[g.f], f32, i - sf) * g.p_in;
             if (cf == g.nf - 2) b += bond_at(gp[g.f], f32, i) * g.p_out;
             bb += b * b;
             na += 1.0;
+            ns += 1.0;
         }
         x[i] = xv;
         dis[i] = dv;
     }
-    double v[2] = {bb, na};
-    const int ops[2] = {RED_SUM, RED_SUM};
-    if (grid_reduce<2, NT>(v, ops, partials, &ss->counter) && threadIdx.x == 0) {
+    double v[3] = {bb, na, ns};
+    const int ops[3] = {RED_SUM, RED_SUM, RED_SUM};
+    if (grid_reduce<3, NT>(v, ops, partials, &ss->counter) && threadIdx.x == 0) {
         ss->bb = v[0];
         ss->n_active = (unsigned long long)v[1];
+        ss->n_solved = (unsigned long long)v[2];
     }
 }
 
@@ -286,7 +389,7 @@ __global__ void unpack_labels_kernel(Geom g, const int *parent, const uint8_t *c
             lab = (int)(rx + (long long)g.nx * ry);
         }
         if (label) label[o] = lab;
-        if (cls_out) cls_out[o] = c;
+        if (cls_out) cls_out[o] = c == CLS_DANGLING ? (uint8_t)CLS_SPANNING : c;
     }
 }
 
@@ -316,6 +419,33 @@ cudaError_t launch_labels(const Geom &g, const void *const graw[3], int f32, int
     if (e != cudaSuccess) return e;
     lab_flags<<<nb, NT, 0, st>>>(g, graw[g.f], f32, parent, flags);
     lab_final<<<nb, NT, 0, st>>>(g, parent, flags, cls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_round(const Geom &g, const void *const graw[3], int f32, const uint8_t *cls,
+                               unsigned int *pr, int *anchor, unsigned int round, unsigned int *count,
+                               cudaStream_t st) {
+    prune_round_kernel<<<blocks_for(grid_nodes(g)), NT, 0, st>>>(g, graw[0], graw[1], graw[2], f32, cls, pr,
+                                                                anchor, round, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_finish(const Geom &g, uint8_t *cls, const unsigned int *pr, int *root,
+                                int passes, cudaStream_t st) {
+    const int nb = blocks_for(grid_nodes(g));
+    prune_mark_kernel<<<nb, NT, 0, st>>>(g, cls, pr);
+    for (int k = 0; k < passes; k++) prune_jump_kernel<<<nb, NT, 0, st>>>(g, pr, root);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_dangling(const Geom &g, const int *root, double *x, cudaStream_t st) {
+    long long nb = blocks_for(grid_nodes(g));
+    fill_dangling_kernel<<<(int)nb, NT, 0, st>>>(g, root, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backbone(const Geom &g, const uint8_t *cls, uint8_t *out, cudaStream_t st) {
+    backbone_kernel<<<blocks_for(grid_nodes(g)), NT, 0, st>>>(g, cls, out);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,7 @@ size_t net_footprint_bytes(const Geom &g, int raw_f32) {
     b += nd * L * 4;                         // scaled FP32 bonds
     b += 7 * L * 4;                          // FP32 inner vectors
     b += L * 4;                              // label flags (set-up only)
+    b += L * 4;                              // dead-end roots (percolated networks)
     return b;
 }
 
@@ -363,6 +364,7 @@ OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_
     const long long side = std::max(n->g.nx, std::max(n->g.ny, n->g.nz));
     o.stag_window = f32 && !rel_mode ? std::max(400LL, 8LL * side) : std::max(4000LL, 64LL * side);
     o.partials = n->partials;
+    o.root = n->proot;
     return o;
 }
 
@@ -463,6 +465,47 @@ net_status autotune_nets(const std::vector<net_t *> &nets, int f32, int default_
 // precision's type, so a switch of precision first re-arms with no correction
 // pending (see solve_impl).
 
+bool prune_enabled() {
+    const char *e = getenv("NETSOLVE_PRUNE");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// Strip the dead-end trees of the spanning clusters (rounds of removing
+// nodes with at most one link left; see prune_round_kernel), then resolve
+// every removed node to the backbone or face node its tree hangs from.  The
+// removed set is exact at any point: stopping after kMaxRounds only leaves
+// deeper trees in the system.  `pr` is a zeroable L-word scratch buffer.
+net_status prune_dead_ends(net_t *n, const void *const gr[3], unsigned int *pr) {
+    constexpr unsigned int kChunk = 16, kMaxRounds = 1u << 14;
+    cudaStream_t st = n->stream;
+    const Geom &G = n->g;
+    const size_t L = (size_t)G.len;
+    CK(cudaMemsetAsync(pr, 0, L * 4, st));
+    CK(dalloc(&n->proot, L * 4, st));
+    CK(cudaMemsetAsync(n->proot, 0xFF, L * 4, st));  // -1: not removed
+    unsigned int round = 0;
+    unsigned long long total = 0;
+    while (round < kMaxRounds) {
+        CK(cudaMemsetAsync(&n->dsc->ss.pruned, 0, sizeof(unsigned int), st));
+        for (unsigned int k = 0; k < kChunk; k++)
+            CK(launch_prune_round(G, gr, n->raw_f32, n->cls, pr, n->proot, ++round, &n->dsc->ss.pruned, st));
+        CK(cudaMemcpyAsync(&n->hsc->ss.pruned, &n->dsc->ss.pruned, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        total += n->hsc->ss.pruned;
+        if (n->hsc->ss.pruned == 0) break;
+    }
+    if (total == 0) {
+        dfree(n->proot, st);
+        n->proot = nullptr;
+        return NET_OK;
+    }
+    int passes = 1;
+    while ((1u << passes) <= round) passes++;
+    CK(launch_prune_finish(G, n->cls, pr, n->proot, passes + 1, st));
+    n->prune_rounds = (int)round;
+    return NET_OK;
+}
+
 net_status setup_network(net_t *n, const void *const g[3], int on_device) {
     cudaStream_t st = n->stream;
     const Geom &G = n->g;
@@ -495,6 +538,10 @@ net_status setup_network(net_t *n, const void *const g[3], int on_device) {
     }
     const void *gr[3] = {n->graw[0], n->graw[1], G.ndim == 3 ? n->graw[2] : n->graw[0]};
     CK(launch_labels(G, gr, n->raw_f32, n->parent, flags, n->cls, st));
+    if (prune_enabled()) {
+        net_status ps = prune_dead_ends(n, gr, flags);
+        if (ps != NET_OK) { dfree(flags, st); dfree(stage, st); return ps; }
+    }
     CK(launch_build_system(G, gr, n->raw_f32, n->cls, n->dis, n->x, &n->dsc->ss, n->partials, st));
     dfree(flags, st);
     dfree(stage, st);
@@ -506,6 +553,7 @@ net_status setup_network(net_t *n, const void *const g[3], int on_device) {
     }
     n->bnorm = std::sqrt(n->hsc->ss.bb);
     n->n_active = (long long)n->hsc->ss.n_active;
+    n->n_solved = (long long)n->hsc->ss.n_solved;
     return NET_OK;
 }
 
@@ -528,6 +576,7 @@ void release_network(net_t *n) {
     dfree(n->ps_bar, st);
     dfree(n->ps_err, st);
     dfree(n->parent, st);
+    dfree(n->proot, st);
     dfree(n->cls, st);
     dfree(n->dis, st);
     dfree(n->x, st);
@@ -755,6 +804,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     r->inner_ms = inner_ms;
     r->inner_launches = launches;
     r->g_eff_err = geff_err(n);
+    r->n_solved = n->n_solved;
     r->status = status;
     n->last = *r;
     n->solved = true;
@@ -887,6 +937,22 @@ NET_API net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int6
     if (cls) CK(cudaMemcpyAsync(cls, dc, (size_t)N, cudaMemcpyDeviceToHost, st));
     dfree(dl, st);
     dfree(dc, st);
+    CK(cudaStreamSynchronize(st));
+    return NET_OK;
+}
+
+NET_API net_status net_get_backbone(net_t *net, uint8_t *backbone, int64_t n) {
+    if (!net || !backbone) { set_error("net_get_backbone: NULL argument"); return NET_EINVAL; }
+    const Geom &G = net->g;
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    if (n < N) { set_error("net_get_backbone: buffer holds %lld < %lld", (long long)n, N); return NET_EINVAL; }
+    DevGuard dg(net->device);
+    cudaStream_t st = net->stream;
+    uint8_t *db = nullptr;
+    CK(dalloc(&db, (size_t)N, st));
+    CK(launch_backbone(G, net->cls, db, st));
+    CK(cudaMemcpyAsync(backbone, db, (size_t)N, cudaMemcpyDeviceToHost, st));
+    dfree(db, st);
     CK(cudaStreamSynchronize(st));
     return NET_OK;
 }

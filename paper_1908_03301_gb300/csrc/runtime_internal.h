@@ -43,6 +43,9 @@ struct net_s {
     int raw_f32 = 0;
     void *graw[3] = {nullptr, nullptr, nullptr};  // padded raw bonds
     int *parent = nullptr;                         // union-find roots (padded index)
+    int *proot = nullptr;                          // dead-end node -> its root (-1 elsewhere);
+                                                   // NULL when nothing was stripped
+    int prune_rounds = 0;
     uint8_t *cls = nullptr;                        // cluster classes
     double *dis = nullptr;                         // D^-1/2 on solved nodes, else 0
     double *x = nullptr;                           // FP64 pressures
@@ -66,7 +69,8 @@ struct net_s {
     net_result last{};
     bool solved = false;
     double bnorm = 0.0;
-    long long n_active = 0;
+    long long n_active = 0;   // nodes of spanning clusters
+    long long n_solved = 0;   // of them, unknowns of the linear system
 };
 
 namespace netsolve {
@@ -134,6 +138,9 @@ InnerArgs inner_args(net_t *n, int f32);
 OuterArgs outer_args(net_t *n, int f32, int apply_corr, int corr_f32, const net_opts &op,
                      int inplace = 0);
 net_status setup_network(net_t *n, const void *const g[3], int on_device);
+// NETSOLVE_PRUNE=0 keeps dead-end trees in the linear system (diagnostics).
+bool prune_enabled();
+net_status prune_dead_ends(net_t *n, const void *const gr[3], unsigned int *pr);
 void release_network(net_t *n);
 net_status create_network(const net_desc *desc, const void *const g[3], net_t **out);
 net_status solve_impl(net_t *n, const net_opts *o, net_result *r);

@@ -43,7 +43,8 @@ class net_result(C.Structure):
                 ("max_imbalance", C.c_double), ("energy_g", C.c_double),
                 ("n_active", C.c_int64), ("outer_iters", C.c_int), ("inner_iters", C.c_int64),
                 ("fp64_fallback", C.c_int), ("ms", C.c_float), ("inner_ms", C.c_float),
-                ("inner_launches", C.c_int64), ("status", C.c_int), ("g_eff_err", C.c_double)]
+                ("inner_launches", C.c_int64), ("status", C.c_int), ("g_eff_err", C.c_double),
+                ("n_solved", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,7 +62,8 @@ class net_tune(C.Structure):
 EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_pressure",
            "net_get_labels", "net_destroy", "net_solve_batch", "netq_create", "netq_submit",
            "netq_poll", "netq_wait", "netq_cancel", "netq_stats", "netq_destroy",
-           "net_last_error", "net_labels_noalloc", "net_autotune", "net_tune_clear"]
+           "net_last_error", "net_labels_noalloc", "net_autotune", "net_tune_clear",
+           "net_get_backbone"]
 
 _lib = None
 
@@ -91,6 +93,8 @@ def lib(build_if_missing: bool = False):
     L.net_get_pressure.restype = C.c_int
     L.net_get_labels.argtypes = [vp, vp, vp, C.c_int64]
     L.net_get_labels.restype = C.c_int
+    L.net_get_backbone.argtypes = [vp, vp, C.c_int64]
+    L.net_get_backbone.restype = C.c_int
     L.net_destroy.argtypes = [vp]
     L.net_destroy.restype = C.c_int
     L.net_last_error.argtypes = []
@@ -225,6 +229,7 @@ class Result:
     inner_launches: int
     status: int
     g_eff_err: float
+    n_solved: int
     error: str = ""  # message of a non-OK status
 
     @classmethod
@@ -286,6 +291,12 @@ class Network:
         _check(lib().net_get_labels(self.h, lab.ctypes.data, cls.ctypes.data, self.N),
                "net_get_labels")
         return lab.reshape(self.shape), cls.reshape(self.shape)
+
+    def backbone(self):
+        """bool mask of the backbone (spanning nodes left in the system)."""
+        b = np.empty(self.N, np.uint8)
+        _check(lib().net_get_backbone(self.h, b.ctypes.data, self.N), "net_get_backbone")
+        return b.reshape(self.shape).astype(bool)
 
     def close(self):
         if getattr(self, "h", None):
