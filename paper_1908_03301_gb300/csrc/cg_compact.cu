@@ -1,0 +1,473 @@
+// cg_compact.cu -- the inner CG solve over a compacted list of unknowns.
+//
+// Near the percolation threshold the unknowns of the linear system (the
+// spanning clusters less their dead-end trees) are a small part of the
+// lattice: 13 % of a 256^3 network at p = 0.26.  A sweep over the lattice
+// then moves mostly zeros.  Here the unknowns are listed in lattice order;
+// each keeps the list indices of its 2d lattice neighbours and the scaled
+// bonds to them (an ELL table stored direction-major, so a warp reads
+// consecutive entries; a missing neighbour is the unknown itself with a zero
+// bond), and y, r, p, q are compact vectors.
+//
+// One cooperative launch runs a whole inner solve.  Iteration k (the same
+// arithmetic as the lattice kernels, Sec. IV):
+//   phase A, every unknown:  r -= alpha q;  y += alpha p;  p = r + beta p
+//                            (iteration 0: p = r, y = 0)
+//   grid barrier
+//   phase B, every unknown:  q = p - sum_j ghat_j p_j  and the sums
+//                            <p,q>, <r,q>, <q,q>, <r,r>
+//   grid barrier: the last CTA to arrive sums the per-CTA partials in CTA
+//   order in FP64, advances the CG state (finish_iteration) and publishes it;
+//   every CTA reads that one record.
+// A thread owns the same unknowns in both phases and in every iteration, so
+// its own entries need no cross-SM visibility; neighbours' p written by other
+// CTAs are read through L2 (ld.global.cg).  Every wait is bounded.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "kernels.h"
+
+namespace netsolve {
+namespace {
+
+constexpr int CT = 512;                 // threads per CTA
+constexpr int CW = CT / 32;
+constexpr int UNR = 2;                  // unknowns a thread keeps in flight
+constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long lattice_index(const Geom &g, long long t) {
+    return g.pad + t;  // t runs over the padded grid (px * ny * nz), row-major
+}
+
+// ------------------------------------------------------------------ build
+// Unknowns per chunk of the lattice.
+__global__ void compact_count_kernel(Geom g, const uint8_t *__restrict__ cls, unsigned int *counts) {
+    __shared__ unsigned int s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const long long n = (long long)g.px * g.ny * g.nz;
+    const long long t0 = (long long)blockIdx.x * SCAN_CHUNK;
+    unsigned int mine = 0;
+    for (int j = threadIdx.x; j < SCAN_CHUNK; j += blockDim.x) {
+        const long long t = t0 + j;
+        if (t < n && cls[lattice_index(g, t)] == CLS_SPANNING) mine++;
+    }
+    atomicAdd(&s, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s;
+}
+
+// List index of every unknown, in lattice order: block b starts at
+// offsets[b]; inside a chunk, thread j takes nodes [8j, 8j+8) and a block
+// scan orders the threads.  cmap[i] = list index or -1; cidx[k] = node.
+__global__ void compact_index_kernel(Geom g, const uint8_t *__restrict__ cls,
+                                     const unsigned int *__restrict__ offsets, int *cmap, int *cidx) {
+    constexpr int PER = SCAN_CHUNK / CT;  // 8
+    __shared__ unsigned int warp_tot[CW];
+    const long long n = (long long)g.px * g.ny * g.nz;
+    const long long t0 = (long long)blockIdx.x * SCAN_CHUNK + (long long)threadIdx.x * PER;
+    unsigned int flags = 0, cnt = 0;
+    for (int j = 0; j < PER; j++) {
+        const long long t = t0 + j;
+        if (t < n && cls[lattice_index(g, t)] == CLS_SPANNING) {
+            flags |= 1u << j;
+            cnt++;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned int before = 0;
+    for (int w = 0; w < warp; w++) before += warp_tot[w];
+    unsigned int k = offsets[blockIdx.x] + before + incl - cnt;
+    for (int j = 0; j < PER; j++) {
+        const long long t = t0 + j;
+        if (t >= n) break;
+        const long long i = lattice_index(g, t);
+        if (flags & (1u << j)) {
+            cmap[i] = (int)k;
+            cidx[k] = (int)i;
+            k++;
+        } else {
+            cmap[i] = -1;
+        }
+    }
+}
+
+// ELL row of every unknown: neighbour list index and scaled bond per
+// direction (slot 2d: +e_d, slot 2d+1: -e_d), direction-major.
+template <typename T>
+__global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ cidx,
+                                   const int *__restrict__ cmap, const T *gs0, const T *gs1, const T *gs2,
+                                   int *nbr, T *val) {
+    const T *gs[3] = {gs0, gs1, gs2};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = cidx[k];
+        for (int d = 0; d < g.ndim; d++) {
+            const long long s = g.stride(d);
+            for (int side = 0; side < 2; side++) {
+                const long long j = side ? i - s : i + s;
+                const T gv = side ? gs[d][j] : gs[d][i];
+                const int m = cmap[j];
+                const bool link = m >= 0 && gv != T(0);
+                const long long slot = (long long)(2 * d + side) * U + k;
+                // no neighbour: the unknown itself with a zero bond, so the
+                // read stays in the warp's own line (one shared zero slot
+                // would draw most gathers of the GPU to a single L2 sector)
+                nbr[slot] = link ? m : (int)k;
+                val[slot] = link ? gv : T(0);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ refinement glue
+template <typename T>
+__global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx, const T *__restrict__ src,
+                                      T *dst) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[cidx[k]];
+}
+
+// x += D^-1/2 y on the unknowns; a pass that ended with stop 6 still owes
+// alpha_k p_k (the recursion continues): fold it in and clear y.
+template <typename T>
+__global__ void compact_correct_kernel(long long U, const int *__restrict__ cidx, const double *__restrict__ dis,
+                                       double *x, T *y, const T *__restrict__ p, const InnerScal *is) {
+    const bool owe = is->stop == 6;
+    const double a = is->alpha;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
+         k += (long long)gridDim.x * blockDim.x) {
+        double d = (double)y[k];
+        if (owe) {
+            d = fma(a, (double)p[k], d);
+            y[k] = T(0);
+        }
+        const long long i = cidx[k];
+        x[i] = fma(dis[i], d, x[i]);
+    }
+}
+
+// ------------------------------------------------------------------ the solve
+// Grid barrier part 1: every CTA's writes are done; thread 0 arrives.
+// Returns (to all threads) whether this CTA arrived last at barrier `target`.
+__device__ __forceinline__ bool barrier_arrive(unsigned *count, unsigned target, int G) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        s_last = arrived == (unsigned)G * target;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+// Grid barrier part 2 for the CTAs that did not arrive last (thread 0 waits
+// for the release); returns false if the wait gave up.
+__device__ __forceinline__ bool barrier_wait(const unsigned *gen, unsigned target) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        // poll with relaxed loads (an acquire per poll would order, and slow,
+        // the memory traffic of the other CTA on this SM), then one acquire
+        bool ok = false;
+        for (uint32_t i = 0; i < SPIN_LIMIT; i++)
+            if (ld_relaxed_u32(gen) >= target) {
+                ok = ld_acquire_u32(gen) >= target;
+                break;
+            }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+__device__ __forceinline__ void barrier_release(unsigned *gen, unsigned target) {
+    __threadfence();
+    st_release_u32(gen, target);
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
+    __shared__ InnerScal st;
+    __shared__ T s_red[CW][4];
+    const int G = gridDim.x, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long U = a.n;
+    T *__restrict__ y = (T *)a.y;
+    T *__restrict__ r = (T *)a.r;
+    T *p = (T *)a.p;
+    T *__restrict__ q = (T *)a.q;
+    const T *__restrict__ val = (const T *)a.val;
+    const int *__restrict__ nbr = a.nbr;
+    unsigned *bar_count = a.bar, *bar_gen = a.bar + 1;
+    if (threadIdx.x == 0) {
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.s);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&st);
+        for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = src[k];
+    }
+    __syncthreads();
+    const long long tid = (long long)c * CT + threadIdx.x, nth = (long long)G * CT;
+    unsigned target = 0;
+    bool bad = false;
+    while (st.stop == 0) {
+        const bool first = st.iter == 0;
+        const T alpha = (T)st.alpha, beta = (T)st.beta;
+        // ---- phase A: finish iteration k-1 (UNR unknowns in flight per thread) ----
+        for (long long k0 = tid; k0 < U; k0 += UNR * nth) {
+            T rk[UNR], pk[UNR], qk[UNR], yk[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; u++) {
+                const long long k = k0 + u * nth;
+                if (k < U) {
+                    rk[u] = r[k];
+                    if (!first) {
+                        pk[u] = p[k];
+                        qk[u] = q[k];
+                        yk[u] = y[k];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; u++) {
+                const long long k = k0 + u * nth;
+                if (k >= U) continue;
+                if (first) {
+                    p[k] = rk[u];
+                    y[k] = T(0);
+                } else {
+                    const T rn = fma(-alpha, qk[u], rk[u]);
+                    r[k] = rn;
+                    y[k] = fma(alpha, pk[u], yk[u]);
+                    p[k] = fma(beta, pk[u], rn);
+                }
+            }
+        }
+        ++target;
+        if (barrier_arrive(bar_count, target, G)) {
+            if (threadIdx.x == 0) barrier_release(bar_gen, target);
+        } else if (!barrier_wait(bar_gen, target)) {
+            bad = true;
+        }
+        __syncthreads();
+        // ---- phase B: q = A p and the four sums ----
+        T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
+        for (long long k0 = tid; k0 < U; k0 += UNR * nth) {
+            int nb_i[UNR][2 * NDIM];
+            T nb_g[UNR][2 * NDIM];
+#pragma unroll
+            for (int u = 0; u < UNR; u++) {
+                const long long k = k0 + u * nth;
+#pragma unroll
+                for (int sl = 0; sl < 2 * NDIM; sl++) {
+                    const long long e = (long long)sl * U + k;
+                    nb_i[u][sl] = k < U ? __ldg(nbr + e) : (int)U;
+                    nb_g[u][sl] = k < U ? __ldg(val + e) : T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; u++) {
+                const long long k = k0 + u * nth;
+                if (k >= U) continue;
+                const T pk = __ldcg(p + k);
+                T nb = T(0);
+#pragma unroll
+                for (int sl = 0; sl < 2 * NDIM; sl++) nb = fma(nb_g[u][sl], __ldcg(p + nb_i[u][sl]), nb);
+                const T qk = pk - nb;
+                q[k] = qk;
+                const T rk = r[k];
+                s_pq = fma(pk, qk, s_pq);
+                s_rq = fma(rk, qk, s_rq);
+                s_qq = fma(qk, qk, s_qq);
+                s_rr = fma(rk, rk, s_rr);
+            }
+        }
+        T t4[4] = {s_pq, s_rq, s_qq, s_rr};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t4[k] += __shfl_xor_sync(0xffffffffu, t4[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; k++) s_red[warp][k] = t4[k];
+        __syncthreads();
+        const int par = (int)(st.iter & 1);
+        if (threadIdx.x == 0) {
+            double tot[4] = {0, 0, 0, 0};
+            for (int w = 0; w < CW; w++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) tot[k] += (double)s_red[w][k];
+            if (bad) tot[0] = tot[1] = tot[2] = tot[3] = NAN;
+#pragma unroll
+            for (int k = 0; k < 4; k++) a.pb[((long long)par * G + c) * 4 + k] = tot[k];
+        }
+        ++target;
+        bool ok = true;
+        if (barrier_arrive(bar_count, target, G)) {
+            // the last CTA: one warp sums the partials (lanes stride over
+            // the CTAs, fixed order, FP64), advances the state, releases
+            if (warp == 0) {
+                __threadfence();
+                double tot[4] = {0, 0, 0, 0};
+                for (int i = lane; i < G; i += 32)
+#pragma unroll
+                    for (int k = 0; k < 4; k++) tot[k] += __ldcg(a.pb + ((long long)par * G + i) * 4 + k);
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+                if (lane == 0) {
+                    // advance the state in place (shared memory) and publish it
+                    st.err = 0;
+                    finish_iteration(&st, st.iter, tot);
+                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&st);
+                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.bc + par);
+                    for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = src[k];
+                    barrier_release(bar_gen, target);
+                }
+            }
+        } else {
+            ok = barrier_wait(bar_gen, target);
+            if (threadIdx.x == 0) {
+                if (!ok) {
+                    st.stop = 5;
+                } else {
+                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.bc + par);
+                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&st);
+                    for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = __ldcg(src + k);
+                }
+            }
+        }
+        if (threadIdx.x == 0 && (bad || !ok)) {
+            atomicExch(a.err, 1);
+            st.stop = 5;
+        }
+        __syncthreads();
+    }
+    if (c == 0 && threadIdx.x == 0) {
+        st.counter = 0u;
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&st);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.s);
+        for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = src[k];
+    }
+}
+
+template <typename T, int NDIM>
+cudaError_t launch_cg_t(const CompactArgs &a, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * 2, st);
+    if (e != cudaSuccess) return e;
+    CompactArgs arg = a;
+    void *params[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CT), params, 0,
+                                       st);
+}
+
+template <typename T, int NDIM>
+int grid_t() {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compact_cg_kernel<T, NDIM>, CT, 0);
+    if (nsm < 1) nsm = 1;
+    if (per < 1) per = 1;
+    return nsm * per;
+}
+
+inline int nb_for(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 152LL * 32 ? 152LL * 32 : b));
+}
+
+}  // namespace
+
+int compact_grid(int ndim, int f32) {
+    if (ndim == 2) return f32 ? grid_t<float, 2>() : grid_t<double, 2>();
+    return f32 ? grid_t<float, 3>() : grid_t<double, 3>();
+}
+
+cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f32, const void *const gs[3],
+                          int *cmap, int *cidx, int *nbr, void *val, cudaStream_t st) {
+    const long long n = (long long)g.px * g.ny * g.nz;
+    const int nblk = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    unsigned int *d_cnt = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_cnt, sizeof(unsigned int) * (size_t)nblk, st);
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned int> cnt((size_t)nblk);
+    compact_count_kernel<<<nblk, 256, 0, st>>>(g, cls, d_cnt);
+    e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(unsigned int) * (size_t)nblk, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        // exclusive scan of the chunk counts (host, fixed order)
+        unsigned long long run = 0;
+        for (int b = 0; b < nblk; b++) {
+            const unsigned int c = cnt[(size_t)b];
+            cnt[(size_t)b] = (unsigned int)run;
+            run += c;
+        }
+        if ((long long)run != U) e = cudaErrorInvalidValue;  // set-up count disagrees
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cnt, cnt.data(), sizeof(unsigned int) * (size_t)nblk, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        compact_index_kernel<<<nblk, CT, 0, st>>>(g, cls, d_cnt, cmap, cidx);
+        if (f32)
+            compact_ell_kernel<float><<<nb_for(U), 256, 0, st>>>(g, U, cidx, cmap, (const float *)gs[0],
+                                                                  (const float *)gs[1], (const float *)gs[2], nbr,
+                                                                  (float *)val);
+        else
+            compact_ell_kernel<double><<<nb_for(U), 256, 0, st>>>(g, U, cidx, cmap, (const double *)gs[0],
+                                                                   (const double *)gs[1], (const double *)gs[2], nbr,
+                                                                   (double *)val);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(d_cnt, st);
+    return e;
+}
+
+cudaError_t launch_compact_gather(long long U, const int *cidx, const void *src, void *dst, int f32,
+                                  cudaStream_t st) {
+    if (f32)
+        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, cidx, (const float *)src, (float *)dst);
+    else
+        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, cidx, (const double *)src, (double *)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_correct(long long U, const int *cidx, const double *dis, double *x, void *y,
+                                   const void *p, const InnerScal *is, int f32, cudaStream_t st) {
+    if (f32)
+        compact_correct_kernel<float><<<nb_for(U), 256, 0, st>>>(U, cidx, dis, x, (float *)y, (const float *)p, is);
+    else
+        compact_correct_kernel<double><<<nb_for(U), 256, 0, st>>>(U, cidx, dis, x, (double *)y, (const double *)p,
+                                                                   is);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_cg(const CompactArgs &a, int ndim, int f32, int grid, cudaStream_t st) {
+    if (ndim == 2) return f32 ? launch_cg_t<float, 2>(a, grid, st) : launch_cg_t<double, 2>(a, grid, st);
+    return f32 ? launch_cg_t<float, 3>(a, grid, st) : launch_cg_t<double, 3>(a, grid, st);
+}
+
+}  // namespace netsolve

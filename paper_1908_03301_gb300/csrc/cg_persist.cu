@@ -62,6 +62,11 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -410,10 +415,12 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             }
         } else if (threadIdx.x == 0) {
             // grid barrier, part 2: wait for the release, read the new state
+            // relaxed polls, then one acquire: an acquire per poll would
+            // order (and slow) this SM's other memory traffic
             bool ok = false;
             for (uint32_t i = 0; i < SPIN_LIMIT; i++) {
-                if (ld_acquire(a.bar_gen) >= target) {
-                    ok = true;
+                if (ld_relaxed(a.bar_gen) >= target) {
+                    ok = ld_acquire(a.bar_gen) >= target;
                     break;
                 }
             }

@@ -75,6 +75,32 @@ int persist_grid(const Geom &g);
 cudaError_t persist_prepare();
 cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st);
 
+// ---- inner solve over a compacted list of unknowns (cg_compact.cu) --------
+struct CompactArgs {
+    long long n;            // unknowns
+    void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each
+    const void *val;        // scaled bonds, direction-major [2 ndim][n] (T)
+    const int *nbr;         // neighbour list indices [2 ndim][n] (no neighbour:
+                            // the unknown itself, with a zero bond)
+    InnerScal *s;           // armed state in, final state out
+    InnerScal *bc;          // state published by the grid barrier [2]
+    double *pb;             // per-CTA partial sums [2][grid][4]
+    unsigned *bar;          // grid barrier: arrivals, generation
+    int *err;               // set when a bounded wait gave up
+};
+int compact_grid(int ndim, int f32);
+// List the unknowns (cls == CLS_SPANNING) in lattice order and build their
+// ELL rows from the scaled lattice bonds gs (T).  cmap: L-entry scratch.
+cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f32, const void *const gs[3],
+                          int *cmap, int *cidx, int *nbr, void *val, cudaStream_t st);
+// dst[k] = src[cidx[k]] (lattice -> list, T)
+cudaError_t launch_compact_gather(long long U, const int *cidx, const void *src, void *dst, int f32,
+                                  cudaStream_t st);
+// x[cidx[k]] += D^-1/2 (y[k] (+ alpha p[k] when the pass ended with stop 6))
+cudaError_t launch_compact_correct(long long U, const int *cidx, const double *dis, double *x, void *y,
+                                   const void *p, const InnerScal *is, int f32, cudaStream_t st);
+cudaError_t launch_compact_cg(const CompactArgs &a, int ndim, int f32, int grid, cudaStream_t st);
+
 // ---- persistent sweep over segmented networks (sweep.cu) -------------------
 struct SweepInst;
 struct SweepSeg;

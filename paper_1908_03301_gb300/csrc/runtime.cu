@@ -186,10 +186,74 @@ bool use_sweep_kernel() {
     return !(e && strcmp(e, "tiled") == 0);
 }
 
-bool use_persist_kernel(const net_t *n, int f32) {
+// The compacted solve replaces the lattice kernels when the unknowns are a
+// small part of the lattice (its list traffic is about twice a lattice
+// sweep's per node): below 35 % of the lattice nodes, or always with
+// NETSOLVE_KERNEL=compact.
+bool use_compact_kernel(const net_t *n, int) {
+    if (n->n_solved <= 0) return false;
     const char *e = getenv("NETSOLVE_KERNEL");
-    if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0)) return false;
+    if (e && strcmp(e, "compact") == 0) return true;
+    if (e && *e) return false;
+    const long long lattice = (long long)n->g.nx * n->g.ny * n->g.nz;
+    return 100 * n->n_solved < 35 * lattice;
+}
+
+bool use_persist_kernel(const net_t *n, int f32) {
+    if (use_compact_kernel(n, f32)) return false;
+    const char *e = getenv("NETSOLVE_KERNEL");
+    if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0 || strcmp(e, "compact") == 0)) return false;
     return persist_applies(n->g, f32);
+}
+
+net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
+    const int k = f32 ? 0 : 1;
+    CompactDev &cd = n->cp[k];
+    if (cd.cidx) return NET_OK;
+    net_status s = ensure_precision(n, f32, st);
+    if (s != NET_OK) return s;
+    const Geom &G = n->g;
+    const long long U = n->n_solved;
+    const size_t es = f32 ? 4 : 8, sl = 2 * (size_t)G.ndim;
+    int *cmap = nullptr;
+    CK(dalloc(&cmap, sizeof(int) * (size_t)G.len, st));
+    CK(cudaMemsetAsync(cmap, 0xFF, sizeof(int) * (size_t)G.len, st));  // -1: not an unknown
+    CK(dalloc(&cd.cidx, sizeof(int) * (size_t)U, st));
+    CK(dalloc(&cd.nbr, sizeof(int) * sl * (size_t)U, st));
+    CK(dalloc(&cd.val, es * sl * (size_t)U, st));
+    CK(dalloc(&cd.vec, es * 4 * (size_t)(U + 1), st));
+    cd.grid = compact_grid(G.ndim, f32);
+    CK(dalloc(&cd.bc, sizeof(InnerScal) * 2, st));
+    CK(dalloc(&cd.pb, sizeof(double) * 2 * 4 * (size_t)cd.grid, st));
+    CK(dalloc(&cd.bar, sizeof(unsigned) * 2, st));
+    CK(dalloc(&cd.err, sizeof(int), st));
+    const void *gs[3] = {n->gs[k][0], n->gs[k][1], n->gs[k][2] ? n->gs[k][2] : n->gs[k][0]};
+    CK(compact_build(G, n->cls, U, f32, gs, cmap, cd.cidx, cd.nbr, cd.val, st));
+    dfree(cmap, st);
+    cd.U = U;
+    CK(cudaStreamSynchronize(st));
+    return NET_OK;
+}
+
+CompactArgs compact_args(net_t *n, int f32) {
+    const int k = f32 ? 0 : 1;
+    CompactDev &cd = n->cp[k];
+    const size_t es = f32 ? 4 : 8, V = (size_t)(cd.U + 1);
+    char *v = (char *)cd.vec;
+    CompactArgs a{};
+    a.n = cd.U;
+    a.y = v;
+    a.r = v + 1 * V * es;
+    a.p = v + 2 * V * es;
+    a.q = v + 3 * V * es;
+    a.val = cd.val;
+    a.nbr = cd.nbr;
+    a.s = &n->dsc->in[k];
+    a.bc = cd.bc;
+    a.pb = cd.pb;
+    a.bar = cd.bar;
+    a.err = cd.err;
+    return a;
 }
 
 net_status ensure_persist(net_t *n) {
@@ -561,6 +625,15 @@ void release_network(net_t *n) {
     if (!n) return;
     cudaStream_t st = n->stream;
     for (int k = 0; k < 2; k++) {
+        CompactDev &cd = n->cp[k];
+        dfree(cd.cidx, st);
+        dfree(cd.nbr, st);
+        dfree(cd.val, st);
+        dfree(cd.vec, st);
+        dfree(cd.bc, st);
+        dfree(cd.pb, st);
+        dfree(cd.bar, st);
+        dfree(cd.err, st);
         if (n->gexec[k]) cudaGraphExecDestroy(n->gexec[k]);
         dfree(n->sw[k].segs, st);
         dfree(n->sw[k].cta, st);
@@ -623,6 +696,30 @@ net_status create_network(const net_desc *desc, const void *const g[3], net_t **
     return NET_OK;
 }
 
+// One refinement pass of the single-network driver: the correction (if
+// apply_corr), the FP64 residual and flows, and the next inner solve armed.
+// For the compacted solve the correction is applied on the list, and the new
+// scaled residual is gathered from the lattice into the list.
+net_status outer_pass_single(net_t *n, int f32, int apply_corr, const net_opts &o, cudaStream_t st) {
+    if (use_compact_kernel(n, f32)) {
+        net_status s = ensure_compact(n, f32, st);
+        if (s != NET_OK) return s;
+        const CompactDev &cd = n->cp[f32 ? 0 : 1];
+        const CompactArgs ca = compact_args(n, f32);
+        if (apply_corr)
+            CK(launch_compact_correct(ca.n, cd.cidx, n->dis, n->x, ca.y, ca.p, ca.s, f32, st));
+        OuterArgs oa = outer_args(n, f32, 0, f32, o, 1);
+        oa.allow_cont = o.refine != NET_REFINE_RESTART && apply_corr;  // correction applied above
+        CK(launch_outer(oa, st));
+        const InnerArgs ia = inner_args(n, f32);
+        CK(launch_compact_gather(ca.n, cd.cidx, ia.r[0], ca.r, f32, st));
+        return NET_OK;
+    }
+    OuterArgs oa = outer_args(n, f32, apply_corr, f32, o, use_persist_kernel(n, f32));
+    CK(launch_outer(oa, st));
+    return NET_OK;
+}
+
 // One solve.  Returns the status and fills *r.
 net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     net_opts o;
@@ -642,7 +739,10 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     }
     net_status s = ensure_precision(n, f32, st);
     if (s != NET_OK) return r->status = s;
-    if (!use_persist_kernel(n, f32)) {
+    if (use_compact_kernel(n, f32)) {
+        s = ensure_compact(n, f32, st);
+        if (s != NET_OK) return r->status = s;
+    } else if (!use_persist_kernel(n, f32)) {
         s = ensure_graph(n, f32, K);
         if (s != NET_OK) return r->status = s;
     }
@@ -666,8 +766,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         }
     }
     // first residual pass (no correction pending)
-    OuterArgs oa = outer_args(n, f32, 0, f32, o, use_persist_kernel(n, f32));
-    CK(launch_outer(oa, st));
+    s = outer_pass_single(n, f32, 0, o, st);
+    if (s != NET_OK) return r->status = s;
     CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const double bn = n->bnorm;
@@ -688,7 +788,20 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         InnerScal *hs = &n->hsc->in[f32 ? 0 : 1];
         InnerScal *ds = &n->dsc->in[f32 ? 0 : 1];
         const int k = f32 ? 0 : 1;
-        if (use_persist_kernel(n, f32)) {
+        if (use_compact_kernel(n, f32)) {
+            // the whole inner solve over the listed unknowns, one cooperative launch
+            const CompactArgs ca = compact_args(n, f32);
+            CK(launch_compact_cg(ca, G.ndim, f32, n->cp[k].grid, st));
+            launches += 1;
+            CK(cudaMemcpyAsync(&n->hsc->perr, ca.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hs, ds, sizeof(InnerScal), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(n->ev[2], st));
+            CK(cudaEventSynchronize(n->ev[2]));
+            if (n->hsc->perr) {
+                set_error("a bounded device wait in the compacted CG kernel gave up");
+                return r->status = NET_ETIMEOUT;
+            }
+        } else if (use_persist_kernel(n, f32)) {
             // the whole inner solve in one cooperative launch
             s = ensure_persist(n);
             if (s != NET_OK) return r->status = s;
@@ -753,8 +866,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
         }
         outer++;
         // apply the correction, new residual; arm the same precision again
-        oa = outer_args(n, f32, 1, f32, o, use_persist_kernel(n, f32));
-        CK(launch_outer(oa, st));
+        s = outer_pass_single(n, f32, 1, o, st);
+        if (s != NET_OK) return r->status = s;
         CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rel = std::sqrt(n->hsc->os.rr) / bn;
@@ -766,13 +879,13 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             fallback = 1;
             s = ensure_precision(n, 0, st);
             if (s != NET_OK) return r->status = s;
-            if (!use_persist_kernel(n, 0)) {
+            if (!use_persist_kernel(n, 0) && !use_compact_kernel(n, 0)) {
                 s = ensure_graph(n, 0, K);
                 if (s != NET_OK) return r->status = s;
             }
             // re-arm the FP64 inner solve from the current x (no correction pending)
-            oa = outer_args(n, 0, 0, 0, o, use_persist_kernel(n, 0));
-            CK(launch_outer(oa, st));
+            s = outer_pass_single(n, 0, 0, o, st);
+            if (s != NET_OK) return r->status = s;
             CK(cudaMemcpyAsync(&n->hsc->os, &n->dsc->os, sizeof(OuterScal), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             rel = std::sqrt(n->hsc->os.rr) / bn;

@@ -25,6 +25,20 @@ inline bool same_shape(const PlanShape &a, const PlanShape &b) {
     return a.wcap == b.wcap && a.hcap == b.hcap && a.seg_per_sm == b.seg_per_sm;
 }
 
+// Compacted inner solve of one precision (cg_compact.cu).
+struct CompactDev {
+    long long U = 0;          // unknowns
+    int *cidx = nullptr;      // list index -> padded lattice index
+    int *nbr = nullptr;       // [2 ndim][U] neighbour list indices
+    void *val = nullptr;      // [2 ndim][U] scaled bonds
+    void *vec = nullptr;      // y, r, p, q, each U + 1 entries
+    InnerScal *bc = nullptr;  // published state [2]
+    double *pb = nullptr;     // partial sums [2][grid][4]
+    unsigned *bar = nullptr;  // barrier words
+    int *err = nullptr;
+    int grid = 0;
+};
+
 // Device-resident scalars of one network (one allocation).
 struct DevScal {
     InnerScal in[2];  // [0] FP32 inner solve, [1] FP64 inner solve
@@ -56,6 +70,7 @@ struct net_s {
     netsolve::DevScal *hsc = nullptr;              // pinned host mirror
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     netsolve::SweepDev sw[2];                      // sweep plan per precision
+    netsolve::CompactDev cp[2];                    // compacted solve per precision
     // whole-solve persistent kernel (2D, FP32): halo rows, partials, grid
     // barrier words, error word
     float *ps_hb = nullptr;

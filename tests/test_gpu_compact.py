@@ -1,0 +1,79 @@
+"""The compacted inner solve (unknowns listed in lattice order, ELL rows, one
+cooperative launch per inner solve): every combination of dimension, inner
+precision and refinement scheme must give the oracle's G_eff and pressures,
+and the same answer as the lattice kernels."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_03301_gb300 import netgen
+
+pytestmark = pytest.mark.gpu
+G_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ns():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1908_03301_gb300 import netsolve
+
+    netsolve.lib(build_if_missing=True)
+    return netsolve
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+CASES = [((45, 38), 0, 0.56, 1), ((33, 52), 1, 0.6, 2), ((26, 21, 19), 0, 0.33, 3),
+         ((20, 24, 27), 2, 0.32, 4), ((70, 66, 64), 1, 0.27, 5), ((17, 15, 16), 0, 1.0, 6)]
+
+
+@pytest.mark.parametrize("dims,f,p,seed", CASES)
+@pytest.mark.parametrize("precision,refine", [(0, 0), (1, 0), (0, 1)])
+def test_compact_matches_oracle(ns, monkeypatch, dims, f, p, seed, precision, refine):
+    monkeypatch.setenv("NETSOLVE_KERNEL", "compact")
+    gen = netgen.rng(9800 + seed)
+    planes = netgen.lognormal_iid(dims, gen)
+    if p < 1.0:
+        planes = netgen.percolate(planes, p, gen)
+    ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13)
+    with ns.Network(dims, planes, flow_axis=f) as net:
+        r = net.solve(ns.make_opts(precision=precision, refine=refine))
+        P = net.pressure()
+    if ref.g_eff == 0.0:
+        assert r.g_eff == 0.0
+        return
+    assert r.status == ns.NET_OK, r
+    assert rel(r.g_eff, ref.g_eff) <= G_TOL
+    assert np.max(np.abs(P - ref.P)) <= 1e-7
+
+
+def test_compact_is_chosen_for_sparse_networks_and_agrees_with_sweep(ns, monkeypatch):
+    """A near-critical 3D network (few unknowns after stripping) takes the
+    compacted solve by default; forcing the lattice sweep gives the same G."""
+    gen = netgen.rng(9900)
+    dims = (60, 58, 56)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.27, gen)
+    with ns.Network(dims, planes) as net:
+        a = net.solve()
+    assert a.n_solved * 100 < 35 * np.prod(dims)
+    assert a.inner_launches <= 2 * a.outer_iters + 2  # one launch per inner solve
+    monkeypatch.setenv("NETSOLVE_KERNEL", "sweep")
+    with ns.Network(dims, planes) as net:
+        b = net.solve()
+    assert b.inner_launches > 10 * a.inner_launches
+    assert rel(a.g_eff, b.g_eff) <= G_TOL
+
+
+def test_compact_repeat_is_bit_identical(ns, monkeypatch):
+    monkeypatch.setenv("NETSOLVE_KERNEL", "compact")
+    gen = netgen.rng(9901)
+    dims = (40, 40, 40)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.3, gen)
+    with ns.Network(dims, planes) as net:
+        a = net.solve()
+        b = net.solve()
+    assert a.g_eff == b.g_eff and a.inner_iters == b.inner_iters
