@@ -4,10 +4,10 @@
 // spanning clusters less their dead-end trees) are a small part of the
 // lattice: 13 % of a 256^3 network at p = 0.26.  A sweep over the lattice
 // then moves mostly zeros.  Here the unknowns are listed in lattice order;
-// each keeps the list indices of its 2d lattice neighbours and the scaled
-// bonds to them (an ELL table stored direction-major, so a warp reads
-// consecutive entries; a missing neighbour is the unknown itself with a zero
-// bond), and y, r, p, q are compact vectors.
+// each keeps its scaled bonds to the +e_d neighbours and the list indices of
+// its y and z neighbours (x neighbours are the adjacent list entries); the
+// table is stored direction-major, so a warp reads consecutive entries, and
+// y, r, p, q are compact vectors.
 //
 // One cooperative launch runs a whole inner solve.  Iteration k (the same
 // arithmetic as the lattice kernels, Sec. IV):
@@ -116,8 +116,15 @@ __global__ void compact_index_kernel(Geom g, const uint8_t *__restrict__ cls,
     }
 }
 
-// ELL row of every unknown: neighbour list index and scaled bond per
-// direction (slot 2d: +e_d, slot 2d+1: -e_d), direction-major.
+// ELL row of every unknown.  In lattice order an unknown's +x neighbour, if
+// it is an unknown, is the next entry of the list, so x needs no index.
+//   val[d][k]  (d < ndim, stride U + 1): scaled bond to the +e_d neighbour if
+//              that node is an unknown, else 0 (val[d][U] = 0);
+//   nbr[2(d-1)][k], nbr[2(d-1)+1][k]  (d >= 1, stride U): list index of the
+//              +e_d / -e_d neighbour.  A missing +e_d neighbour is k itself
+//              (its bond is 0); a missing -e_d neighbour is ~k (negative):
+//              the -e_d bond is read from that neighbour's val[d] entry.
+// The -x bond of k is val[0][k-1]: non-zero only if entry k-1 is the -x node.
 template <typename T>
 __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ cidx,
                                    const int *__restrict__ cmap, const T *gs0, const T *gs1, const T *gs2,
@@ -128,18 +135,16 @@ __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ 
         const long long i = cidx[k];
         for (int d = 0; d < g.ndim; d++) {
             const long long s = g.stride(d);
-            for (int side = 0; side < 2; side++) {
-                const long long j = side ? i - s : i + s;
-                const T gv = side ? gs[d][j] : gs[d][i];
-                const int m = cmap[j];
-                const bool link = m >= 0 && gv != T(0);
-                const long long slot = (long long)(2 * d + side) * U + k;
-                // no neighbour: the unknown itself with a zero bond, so the
-                // read stays in the warp's own line (one shared zero slot
-                // would draw most gathers of the GPU to a single L2 sector)
-                nbr[slot] = link ? m : (int)k;
-                val[slot] = link ? gv : T(0);
-            }
+            const T gp = gs[d][i];
+            const int mp = cmap[i + s];
+            const bool lp = mp >= 0 && gp != T(0);
+            val[(long long)d * (U + 1) + k] = lp ? gp : T(0);
+            if (d == 0) continue;
+            const T gm = gs[d][i - s];
+            const int mm = cmap[i - s];
+            const bool lm = mm >= 0 && gm != T(0);
+            nbr[(long long)(2 * (d - 1)) * U + k] = lp ? mp : (int)k;
+            nbr[(long long)(2 * (d - 1) + 1) * U + k] = lm ? mm : ~(int)k;
         }
     }
 }
@@ -274,17 +279,22 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
         __syncthreads();
         // ---- phase B: q = A p and the four sums ----
         T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
+        const long long VS = U + 1;  // val slot stride
         for (long long k0 = tid; k0 < U; k0 += UNR * nth) {
-            int nb_i[UNR][2 * NDIM];
-            T nb_g[UNR][2 * NDIM];
+            T wxp[UNR], wxm[UNR], wp[UNR][NDIM - 1];
+            int ip[UNR][NDIM - 1], im[UNR][NDIM - 1];
 #pragma unroll
             for (int u = 0; u < UNR; u++) {
                 const long long k = k0 + u * nth;
+                const bool ok = k < U;
+                const long long kk = ok ? k : 0;
+                wxp[u] = ok ? __ldg(val + kk) : T(0);
+                wxm[u] = (ok && k > 0) ? __ldg(val + kk - 1) : T(0);
 #pragma unroll
-                for (int sl = 0; sl < 2 * NDIM; sl++) {
-                    const long long e = (long long)sl * U + k;
-                    nb_i[u][sl] = k < U ? __ldg(nbr + e) : (int)U;
-                    nb_g[u][sl] = k < U ? __ldg(val + e) : T(0);
+                for (int d = 1; d < NDIM; d++) {
+                    wp[u][d - 1] = ok ? __ldg(val + d * VS + kk) : T(0);
+                    ip[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1)) * U + kk) : (int)kk;
+                    im[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + kk) : ~(int)kk;
                 }
             }
 #pragma unroll
@@ -292,9 +302,16 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 const long long k = k0 + u * nth;
                 if (k >= U) continue;
                 const T pk = __ldcg(p + k);
-                T nb = T(0);
+                T nb = wxp[u] * __ldcg(p + k + 1);
+                nb = fma(wxm[u], __ldcg(p + (k > 0 ? k - 1 : 0)), nb);
 #pragma unroll
-                for (int sl = 0; sl < 2 * NDIM; sl++) nb = fma(nb_g[u][sl], __ldcg(p + nb_i[u][sl]), nb);
+                for (int d = 1; d < NDIM; d++) {
+                    nb = fma(wp[u][d - 1], __ldcg(p + ip[u][d - 1]), nb);
+                    const int jm = im[u][d - 1];
+                    const int jj = jm >= 0 ? jm : ~jm;
+                    const T wm = jm >= 0 ? __ldg(val + d * VS + jj) : T(0);
+                    nb = fma(wm, __ldcg(p + jj), nb);
+                }
                 const T qk = pk - nb;
                 q[k] = qk;
                 const T rk = r[k];

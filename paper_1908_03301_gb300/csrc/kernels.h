@@ -79,9 +79,9 @@ cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st);
 struct CompactArgs {
     long long n;            // unknowns
     void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each
-    const void *val;        // scaled bonds, direction-major [2 ndim][n] (T)
-    const int *nbr;         // neighbour list indices [2 ndim][n] (no neighbour:
-                            // the unknown itself, with a zero bond)
+    const void *val;        // scaled +e_d bonds [ndim][n + 1] (T; 0: none)
+    const int *nbr;         // list indices of the +-e_d neighbours, d = y[, z]:
+                            // [2 (ndim - 1)][n]; none: k (+e_d), ~k (-e_d)
     InnerScal *s;           // armed state in, final state out
     InnerScal *bc;          // state published by the grid barrier [2]
     double *pb;             // per-CTA partial sums [2][grid][4]

@@ -214,13 +214,13 @@ net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
     if (s != NET_OK) return s;
     const Geom &G = n->g;
     const long long U = n->n_solved;
-    const size_t es = f32 ? 4 : 8, sl = 2 * (size_t)G.ndim;
+    const size_t es = f32 ? 4 : 8, nd = (size_t)G.ndim;
     int *cmap = nullptr;
     CK(dalloc(&cmap, sizeof(int) * (size_t)G.len, st));
     CK(cudaMemsetAsync(cmap, 0xFF, sizeof(int) * (size_t)G.len, st));  // -1: not an unknown
     CK(dalloc(&cd.cidx, sizeof(int) * (size_t)U, st));
-    CK(dalloc(&cd.nbr, sizeof(int) * sl * (size_t)U, st));
-    CK(dalloc(&cd.val, es * sl * (size_t)U, st));
+    CK(dalloc(&cd.nbr, sizeof(int) * 2 * (nd - 1) * (size_t)U, st));
+    CK(dalloc(&cd.val, es * nd * (size_t)(U + 1), st));
     CK(dalloc(&cd.vec, es * 4 * (size_t)(U + 1), st));
     cd.grid = compact_grid(G.ndim, f32);
     CK(dalloc(&cd.bc, sizeof(InnerScal) * 2, st));

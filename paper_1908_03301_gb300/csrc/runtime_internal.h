@@ -29,8 +29,8 @@ inline bool same_shape(const PlanShape &a, const PlanShape &b) {
 struct CompactDev {
     long long U = 0;          // unknowns
     int *cidx = nullptr;      // list index -> padded lattice index
-    int *nbr = nullptr;       // [2 ndim][U] neighbour list indices
-    void *val = nullptr;      // [2 ndim][U] scaled bonds
+    int *nbr = nullptr;       // [2 (ndim - 1)][U] y/z neighbour list indices
+    void *val = nullptr;      // [ndim][U + 1] scaled +e_d bonds
     void *vec = nullptr;      // y, r, p, q, each U + 1 entries
     InnerScal *bc = nullptr;  // published state [2]
     double *pb = nullptr;     // partial sums [2][grid][4]
