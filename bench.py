@@ -53,6 +53,8 @@ def args_():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--fp64", action="store_true",
+                    help="with --profile-solve: an FP64 inner loop instead of FP32")
     ap.add_argument("--profile-solve", action="store_true",
                     help="one set-up and one refinement step on the workload, printing the inner "
                          "iteration count (for normalising profiler counters per iteration)")
@@ -367,10 +369,11 @@ def run_profile_solve(a):
         dims, planes = netgen.workload_fbm2d(n=a.size)
     tplanes = [torch.from_numpy(g).cuda() for g in planes]
     net = ns.Network(dims, tplanes)
-    r = net.solve(ns.make_opts(max_outer=1, tol_rel=TOL_REL), check=False)
+    prec = ns.NET_FP64 if a.fp64 else ns.NET_MIXED
+    r = net.solve(ns.make_opts(precision=prec, max_outer=1, tol_rel=TOL_REL), check=False)
     net.close()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_solve": True, "dims": list(dims), "inner_iters": r.inner_iters,
+    print(json.dumps({"profile_solve": True, "fp64": a.fp64, "dims": list(dims), "inner_iters": r.inner_iters,
                       "inner_ms": r.inner_ms, "n_active": r.n_active, "n_solved": r.n_solved,
                       "inner_launches": r.inner_launches}), flush=True)
 

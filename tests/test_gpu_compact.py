@@ -77,3 +77,43 @@ def test_compact_repeat_is_bit_identical(ns, monkeypatch):
         a = net.solve()
         b = net.solve()
     assert a.g_eff == b.g_eff and a.inner_iters == b.inner_iters
+
+
+@pytest.mark.parametrize("dims,planes_fn", [
+    ((3, 1), lambda d: netgen.uniform(d, 2.0)),                       # one unknown
+    ((4, 1), lambda d: netgen.uniform(d, 1.0)),                       # a chain of two
+    ((5, 4), lambda d: netgen.lognormal_iid(d, netgen.rng(1))),
+    ((3, 3, 3), lambda d: netgen.lognormal_iid(d, netgen.rng(2))),
+    ((9, 7), lambda d: netgen.percolate(netgen.lognormal_iid(d, netgen.rng(3)), 0.6, netgen.rng(4))),
+])
+def test_compact_tiny_networks(ns, monkeypatch, dims, planes_fn):
+    """Far fewer unknowns than threads in the cooperative grid (down to one)."""
+    monkeypatch.setenv("NETSOLVE_KERNEL", "compact")
+    planes = planes_fn(dims)
+    ref = oracle.solve(dims, planes, tol=1e-13)
+    for precision in (0, 1):
+        with ns.Network(dims, planes) as net:
+            r = net.solve(ns.make_opts(precision=precision))
+            P = net.pressure()
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+            continue
+        assert r.status == ns.NET_OK, r
+        assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        assert np.max(np.abs(P - ref.P)) <= 1e-7
+
+
+def test_compact_capped_solve_resumes(ns, monkeypatch):
+    """A solve stopped by max_outer leaves consistent pressures; the next
+    solve, started from them, converges to the oracle."""
+    monkeypatch.setenv("NETSOLVE_KERNEL", "compact")
+    gen = netgen.rng(9910)
+    dims = (30, 28, 26)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.33, gen)
+    ref = oracle.solve(dims, planes, tol=1e-13)
+    with ns.Network(dims, planes) as net:
+        a = net.solve(ns.make_opts(max_outer=1), check=False)
+        P1 = net.pressure()
+        b = net.solve(x0=P1)
+    assert a.outer_iters == 1
+    assert b.status == ns.NET_OK and rel(b.g_eff, ref.g_eff) <= G_TOL
