@@ -84,6 +84,9 @@ struct F4 {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.f; }
+    __device__ __forceinline__ void st_keep(float *p, uint64_t pol) const {
+        st_hint_f4(p, v[0], v[1], v[2], v[3], pol);
+    }
 };
 
 // halo buffer row (parity, cta, edge, array) in global memory
@@ -92,10 +95,14 @@ __device__ __forceinline__ float *hb_row(const PersistArgs &a, int par, int cta,
     return a.hb + ((((long long)par * G + cta) * 2 + e) * 3 + arr) * px;
 }
 
-// Producer: issue the row stage of step t (t = -1 .. n-1) of a sweep.
+// Producer: issue the row stage of step t (t = -1 .. n-1) of a sweep.  The
+// vectors y, r, p, q are read and written every iteration (67 MB at 2048^2):
+// they are loaded and stored with an evict-last L2 policy, which keeps them in
+// the persisting part of L2 that the host sets aside for the solve; the bond
+// planes (read only) stream.
 __device__ __forceinline__ void issue_row_stage(unsigned char *smem, uint64_t *full, int b, int t,
                                                 int row0, int row1, int px, bool first,
-                                                const PersistArgs &a, int lane) {
+                                                const PersistArgs &a, int lane, uint64_t pol) {
     const uint32_t rb = (uint32_t)px * 4u;
     const int me = row0 + t + 1, mt = row0 + t;
     const int nl = me < row1 ? (first ? 1 : 4) : 0;  // r [q p y] of row me
@@ -105,7 +112,7 @@ __device__ __forceinline__ void issue_row_stage(unsigned char *smem, uint64_t *f
     const long long base = a.g.pad;
     if (lane < nl) {
         const float *src = lane == 0 ? a.r : (lane == 1 ? a.q : (lane == 2 ? a.p : a.y));
-        bulk_load(stg(smem, b, lane), src + base + (long long)me * px, rb, &full[b]);
+        bulk_load_hint(stg(smem, b, lane), src + base + (long long)me * px, rb, &full[b], pol);
     } else if (lane >= 8 && lane < 8 + nb) {
         const int which = nb == 1 ? A_GY : (lane == 8 ? A_GX : A_GY);
         bulk_load(stg(smem, b, which), (which == A_GX ? a.gx : a.gy) + base + (long long)mt * px, rb,
@@ -142,6 +149,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
     }
     __syncthreads();
 
+    const uint64_t keep = l2_policy_keep();
     // producer state
     long long P_step = 0;  // row stages issued (all sweeps)
     int pre = 0;           // stages of the coming sweep already issued
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             if (!ok) plim = 1024;
             fence_proxy_async_smem();
         }
-        issue_row_stage(smem, full, b, t, row0, row1, px, first, a, lane);
+        issue_row_stage(smem, full, b, t, row0, row1, px, first, a, lane, keep);
         P_step++;
     };
 
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                             pn = rv;
                             F4 z;
                             z.zero();
-                            z.st(a.y + i);
+                            z.st_keep(a.y + i, keep);
                         } else {
                             F4 qv, pv, yv;
                             qv.ld(sq + cx);
@@ -262,10 +270,10 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                                 pn.v[k] = pnew(r_next.v[k], pv.v[k], beta);
                                 yv.v[k] = fmaf(alpha, pv.v[k], yv.v[k]);
                             }
-                            yv.st(a.y + i);
+                            yv.st_keep(a.y + i, keep);
                         }
-                        r_next.st(a.r + i);
-                        pn.st(a.p + i);
+                        r_next.st_keep(a.r + i, keep);
+                        pn.st_keep(a.p + i, keep);
                         if (me == row0) {
                             r_next.st(hb_row(a, par, c, 0, H_R, G, px) + cx);
                             pn.st(hb_row(a, par, c, 0, H_P, G, px) + cx);
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                             a_qq = fmaf(qk, qk, a_qq);
                             a_rr = fmaf(r_cur.v[k], r_cur.v[k], a_rr);
                         }
-                        qv.st(a.q + base + (long long)mt * px + cx);
+                        qv.st_keep(a.q + base + (long long)mt * px + cx, keep);
                         if (mt == row0) qv.st(hb_row(a, par, c, 0, H_Q, G, px) + cx);
                         if (mt == row1 - 1) qv.st(hb_row(a, par, c, 1, H_Q, G, px) + cx);
                     }

@@ -696,6 +696,33 @@ net_status create_network(const net_desc *desc, const void *const g[3], net_t **
     return NET_OK;
 }
 
+// L2 set-aside for the persistent kernel's vectors (see cg_persist.cu): a
+// per-context limit, set for the duration of one solve and put back to 0
+// (with the persisting lines reset) before the solve returns, so nothing of
+// it outlasts the call and later work sees the whole L2 again.
+// NETSOLVE_L2_KEEP=0 leaves the limit alone.
+struct L2Keep {
+    bool on = false;
+    void begin(const net_t *n) {
+        const char *e = getenv("NETSOLVE_L2_KEEP");
+        if (e && strcmp(e, "0") == 0) return;
+        int maxp = 0;
+        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, n->device) != cudaSuccess ||
+            maxp <= 0)
+            return;
+        size_t want = (size_t)4 * (size_t)n->g.len * sizeof(float);  // y, r, p, q
+        if (want > (size_t)maxp) want = (size_t)maxp;
+        on = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess;
+    }
+    void end() {
+        if (!on) return;
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+        on = false;
+    }
+    ~L2Keep() { end(); }
+};
+
 // One refinement pass of the single-network driver: the correction (if
 // apply_corr), the FP64 residual and flows, and the next inner solve armed.
 // For the compacted solve the correction is applied on the list, and the new
@@ -780,6 +807,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     net_status status = NET_OK;
     Progress prog;
     prog.start(rel, geff_err(n));
+    L2Keep l2keep;
+    if (use_persist_kernel(n, f32) && dist > 1.0 && bn != 0.0) l2keep.begin(n);
     while (true) {
         if (dist <= 1.0 || bn == 0.0) break;
         if (outer >= o.max_outer) { status = NET_ENOTCONVERGED; break; }
@@ -895,6 +924,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     }
     CK(cudaEventRecord(n->ev[2], st));
     CK(cudaEventSynchronize(n->ev[2]));
+    l2keep.end();
     float total_ms = 0.f;
     CK(cudaEventElapsedTime(&total_ms, n->ev[0], n->ev[2]));
     const OuterScal &os = n->hsc->os;
