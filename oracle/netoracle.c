@@ -11,8 +11,9 @@
  *   * Eq. 3:   mass balance sum_j q_ij = 0 at every interior node gives the
  *     linear system G P = b; b collects the bonds to the fixed-pressure faces.
  *   * Sec. II: a fixed pressure drop along one axis (faces x_f = 0 at p_in and
- *     x_f = n_f-1 at p_out).  The transverse boundaries are no-flow (the
- *     planes simply have no bond beyond the last node).
+ *     x_f = n_f-1 at p_out).  Each transverse boundary is either no-flow (the
+ *     plane has no bond beyond the last node) or periodic, as the paper
+ *     states (the last layer's bonds connect to the first layer).
  *   * Eq. 4:   K = (Q/S)(mu L / dP) with Q the total inlet flow, in lattice
  *     units mu = 1, L = n_f - 1, S = product of the transverse node counts.
  *   * Sec. II / IV: G P = b solved by conjugate gradients; the preconditioner
@@ -28,7 +29,8 @@
  *
  * Layout: node (x,y,z) has linear index x + nx*(y + ny*z).  Bond plane d holds
  * the bond from node c to c + e_d; its extents are the node extents with n_d
- * reduced by one, indexed the same way.
+ * reduced by one (n_d itself for a periodic axis, whose last layer holds the
+ * bonds that wrap to the first), indexed the same way.
  *
  * Sums over nodes use a fixed split into ORC_NCHUNK pieces added in order, so
  * results do not depend on the OpenMP thread count.
@@ -48,6 +50,7 @@ typedef struct {
     int64_t n[3];      /* node extents; n[2] = 1 in 2D */
     int flow_axis;     /* axis of the imposed pressure drop */
     double p_in, p_out;
+    unsigned periodic; /* bit d: axis d is periodic (never the flow axis) */
 } or_desc;
 
 typedef struct {
@@ -80,9 +83,17 @@ static int64_t node_index(const or_desc *d, const int64_t c[3]) {
     return c[0] + d->n[0] * (c[1] + d->n[1] * c[2]);
 }
 
+static int periodic(const or_desc *d, int dir) { return (d->periodic >> dir) & 1u; }
+
+/* Extent of bond plane dir along axis a: one bond fewer than nodes along dir,
+ * unless dir is periodic (the last layer's bonds wrap to the first layer). */
+static int64_t plane_extent(const or_desc *d, int dir, int a) {
+    return d->n[a] - (a == dir && !periodic(d, dir));
+}
+
 /* Conductance of the bond from node c to c + e_dir (the bond must exist). */
 static double bond(const or_desc *d, const double *const g[3], int dir, const int64_t c[3]) {
-    int64_t m0 = d->n[0] - (dir == 0), m1 = d->n[1] - (dir == 1);
+    int64_t m0 = plane_extent(d, dir, 0), m1 = plane_extent(d, dir, 1);
     return g[dir][c[0] + m0 * (c[1] + m1 * c[2])];
 }
 
@@ -104,12 +115,12 @@ static int neighbour(const or_desc *d, const double *const g[3], const int64_t c
     int dir = k / 2;
     int64_t cc[3] = {c[0], c[1], c[2]};
     if ((k & 1) == 0) {
-        if (c[dir] + 1 >= d->n[dir]) return 0;
+        if (c[dir] + 1 >= d->n[dir] && !periodic(d, dir)) return 0;
         *gij = bond(d, g, dir, c);
-        cc[dir] += 1;
+        cc[dir] = (c[dir] + 1) % d->n[dir];
     } else {
-        if (c[dir] == 0) return 0;
-        cc[dir] -= 1;
+        if (c[dir] == 0 && !periodic(d, dir)) return 0;
+        cc[dir] = (c[dir] + d->n[dir] - 1) % d->n[dir];
         *gij = bond(d, g, dir, cc);
     }
     *j = node_index(d, cc);
@@ -123,11 +134,15 @@ static int validate(const or_desc *d, const double *const g[3]) {
     if (d->ndim == 2 && d->n[2] != 1) return -1;
     if (d->flow_axis < 0 || d->flow_axis >= d->ndim) return -1;
     if (d->n[d->flow_axis] < 3) return -1;
+    if (d->periodic >> d->ndim) return -1;
+    if (periodic(d, d->flow_axis)) return -1;
+    for (int dir = 0; dir < d->ndim; dir++)
+        if (periodic(d, dir) && d->n[dir] < 3) return -1;
     if (!isfinite(d->p_in) || !isfinite(d->p_out)) return -1;
     if (n_nodes(d) >= ((int64_t)1 << 31)) return -1;
     for (int dir = 0; dir < d->ndim; dir++) {
         int64_t m = 1;
-        for (int a = 0; a < 3; a++) m *= d->n[a] - (a == dir);
+        for (int a = 0; a < 3; a++) m *= plane_extent(d, dir, a);
         for (int64_t b = 0; b < m; b++) {
             double v = g[dir][b];
             if (!(v >= 0.0) || !isfinite(v)) return -1;

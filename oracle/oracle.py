@@ -25,7 +25,7 @@ CLS_ISOLATED, CLS_INLET, CLS_OUTLET, CLS_SPANNING, CLS_FACE_IN, CLS_FACE_OUT = r
 
 class _Desc(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 3), ("flow_axis", C.c_int),
-                ("p_in", C.c_double), ("p_out", C.c_double)]
+                ("p_in", C.c_double), ("p_out", C.c_double), ("periodic", C.c_uint)]
 
 
 class _Res(C.Structure):
@@ -86,14 +86,24 @@ def _load():
     return _lib
 
 
-def _prep(dims, planes, flow_axis, p_in, p_out):
+def _mask(periodic):
+    """Axes (iterable of 0/1/2) -> bit mask."""
+    m = 0
+    for a in periodic:
+        m |= 1 << int(a)
+    return m
+
+
+def _prep(dims, planes, flow_axis, p_in, p_out, periodic=()):
     ndim = len(dims)
     n = list(int(v) for v in dims) + [1] * (3 - ndim)
-    desc = _Desc(ndim, (C.c_int64 * 3)(*n), int(flow_axis), float(p_in), float(p_out))
+    mask = _mask(periodic)
+    desc = _Desc(ndim, (C.c_int64 * 3)(*n), int(flow_axis), float(p_in), float(p_out), mask)
     arrs = []
     for d in range(ndim):
         want = list(n)
-        want[d] -= 1
+        if not (mask >> d) & 1:
+            want[d] -= 1
         a = np.ascontiguousarray(planes[d], dtype=np.float64)
         if a.size != int(np.prod(want)):
             raise ValueError(f"bond plane {d} has {a.size} entries, expected {int(np.prod(want))}")
@@ -106,10 +116,12 @@ def _prep(dims, planes, flow_axis, p_in, p_out):
     return desc, ptrs, arrs, N, shape
 
 
-def labels(dims, planes, flow_axis=0):
-    """Canonical cluster labels (int32) and classes (uint8), node-shaped."""
+def labels(dims, planes, flow_axis=0, periodic=()):
+    """Canonical cluster labels (int32) and classes (uint8), node-shaped.
+    ``periodic``: transverse axes with periodic boundaries (their bond planes
+    have the full node extent along that axis)."""
     lib = _load()
-    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0, periodic)
     lab = np.empty(N, np.int32)
     cls = np.empty(N, np.uint8)
     if lib.or_labels(C.byref(desc), ptrs, lab.ctypes.data, cls.ctypes.data) != 0:
@@ -117,21 +129,21 @@ def labels(dims, planes, flow_axis=0):
     return lab.reshape(shape), cls.reshape(shape)
 
 
-def backbone(dims, planes, flow_axis=0):
+def backbone(dims, planes, flow_axis=0, periodic=()):
     """Spanning-cluster nodes left after stripping dead-end trees (bool,
     node-shaped); every other node is False."""
     lib = _load()
-    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0, periodic)
     out = np.empty(N, np.uint8)
     if lib.or_backbone(C.byref(desc), ptrs, out.ctypes.data) != 0:
         raise ValueError("invalid network")
     return out.reshape(shape).astype(bool)
 
 
-def residual(dims, planes, P, flow_axis=0):
+def residual(dims, planes, P, flow_axis=0, periodic=()):
     """Nodal imbalance sum_j g_ij (P_j - P_i) at interior nodes (0 on faces)."""
     lib = _load()
-    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0)
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0, periodic)
     Pc = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
     out = np.empty(N, np.float64)
     if lib.or_residual(C.byref(desc), ptrs, Pc.ctypes.data, out.ctypes.data) != 0:
@@ -140,10 +152,10 @@ def residual(dims, planes, P, flow_axis=0):
 
 
 def solve(dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, tol=1e-13, max_iter=10**7,
-          nthreads=0) -> OracleResult:
+          nthreads=0, periodic=()) -> OracleResult:
     """FP64 Jacobi-PCG solve of Eq. 3 plus the flows of Eq. 4."""
     lib = _load()
-    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, p_in, p_out)
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, p_in, p_out, periodic)
     P = np.empty(N, np.float64)
     lab = np.empty(N, np.int32)
     cls = np.empty(N, np.uint8)

@@ -41,15 +41,18 @@ def node_shape(dims):
     return tuple(reversed(tuple(int(v) for v in dims)))
 
 
-def plane_shape(dims, d):
-    """numpy shape of bond plane ``d`` (0 = x, 1 = y, 2 = z)."""
+def plane_shape(dims, d, periodic=()):
+    """numpy shape of bond plane ``d`` (0 = x, 1 = y, 2 = z).  Along a
+    periodic axis the plane has one bond per node: the last one wraps to the
+    first layer."""
     n = list(int(v) for v in dims)
-    n[d] -= 1
+    if d not in periodic:
+        n[d] -= 1
     return tuple(reversed(n))
 
 
-def n_bonds(dims):
-    return [int(np.prod(plane_shape(dims, d))) for d in range(len(dims))]
+def n_bonds(dims, periodic=()):
+    return [int(np.prod(plane_shape(dims, d, periodic))) for d in range(len(dims))]
 
 
 def _node_to_bonds(field, dims):
@@ -69,18 +72,21 @@ def _node_to_bonds(field, dims):
 # --------------------------------------------------------------------------
 # elementary fields
 # --------------------------------------------------------------------------
-def uniform(dims, value=1.0, dtype=np.float64):
-    return [np.full(plane_shape(dims, d), value, dtype=dtype) for d in range(len(dims))]
+def uniform(dims, value=1.0, dtype=np.float64, periodic=()):
+    return [np.full(plane_shape(dims, d, periodic), value, dtype=dtype)
+            for d in range(len(dims))]
 
 
-def loguniform_iid(dims, gen, lo=-1.0, hi=1.0):
+def loguniform_iid(dims, gen, lo=-1.0, hi=1.0, periodic=()):
     """g = 10**U(lo, hi), i.i.d. per bond."""
-    return [10.0 ** gen.uniform(lo, hi, size=plane_shape(dims, d)) for d in range(len(dims))]
+    return [10.0 ** gen.uniform(lo, hi, size=plane_shape(dims, d, periodic))
+            for d in range(len(dims))]
 
 
-def lognormal_iid(dims, gen, sigma=1.0):
+def lognormal_iid(dims, gen, sigma=1.0, periodic=()):
     """g = exp(sigma * N(0,1)), i.i.d. per bond."""
-    return [np.exp(sigma * gen.standard_normal(plane_shape(dims, d))) for d in range(len(dims))]
+    return [np.exp(sigma * gen.standard_normal(plane_shape(dims, d, periodic)))
+            for d in range(len(dims))]
 
 
 def stratified_layers(dims, gen, sigma=1.0):

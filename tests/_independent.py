@@ -21,21 +21,25 @@ def node_coords(dims):
     return idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1]), n
 
 
-def bond_list(dims, planes):
-    """All bonds as (i, j, g) with j = i + e_d."""
+def bond_list(dims, planes, periodic=()):
+    """All bonds as (i, j, g) with j the node one step along e_d; along a
+    periodic axis the last layer's bonds reach back to layer 0."""
     n = list(dims) + [1] * (3 - len(dims))
     out = []
     for d in range(len(dims)):
         m = list(n)
-        m[d] -= 1
+        if d not in periodic:
+            m[d] -= 1
         g = np.asarray(planes[d], dtype=np.float64).reshape(-1)
         for z in range(m[2]):
             for y in range(m[1]):
                 for x in range(m[0]):
                     b = x + m[0] * (y + m[1] * z)
-                    i = x + n[0] * (y + n[1] * z)
-                    step = [1, n[0], n[0] * n[1]][d]
-                    out.append((i, i + step, float(g[b])))
+                    c = [x, y, z]
+                    i = c[0] + n[0] * (c[1] + n[1] * c[2])
+                    c[d] = (c[d] + 1) % n[d]
+                    j = c[0] + n[0] * (c[1] + n[1] * c[2])
+                    out.append((i, j, float(g[b])))
     return out
 
 
@@ -48,11 +52,11 @@ def face_kind(dims, flow_axis):
     return kind
 
 
-def bfs_labels(dims, planes, flow_axis=0):
+def bfs_labels(dims, planes, flow_axis=0, periodic=()):
     kind = face_kind(dims, flow_axis)
     N = len(kind)
     adj = [[] for _ in range(N)]
-    for i, j, g in bond_list(dims, planes):
+    for i, j, g in bond_list(dims, planes, periodic):
         if g > 0:
             adj[i].append(j)
             adj[j].append(i)
@@ -84,12 +88,12 @@ def bfs_labels(dims, planes, flow_axis=0):
     return label, cls
 
 
-def dense_solve(dims, planes, flow_axis=0, p_in=1.0, p_out=0.0):
+def dense_solve(dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, periodic=()):
     """Returns (P, Q_in, Q_out) by a dense direct solve on the spanning set."""
     kind = face_kind(dims, flow_axis)
-    label, cls = bfs_labels(dims, planes, flow_axis)
+    label, cls = bfs_labels(dims, planes, flow_axis, periodic)
     N = len(kind)
-    bonds = bond_list(dims, planes)
+    bonds = bond_list(dims, planes, periodic)
     B = np.zeros((len(bonds), N))
     w = np.zeros(len(bonds))
     for k, (i, j, g) in enumerate(bonds):

@@ -248,13 +248,13 @@ def test_invalid_inputs_rejected():
 
 
 # ---------------------------------------------------------------- backbone (dead-end stripping)
-def _nx_backbone(dims, planes, flow_axis=0):
+def _nx_backbone(dims, planes, flow_axis=0, periodic=()):
     """Backbone by networkx's k-core: the graph of open bonds among the
     spanning nodes and the face nodes (face-face bonds left out), every face
     node tied to a triangle so that it never drops below degree 2 while it
     keeps one interior link.  The 2-core's interior nodes are the backbone."""
     nx = pytest.importorskip("networkx")
-    lab, cls = oracle.labels(dims, planes, flow_axis)
+    lab, cls = oracle.labels(dims, planes, flow_axis, periodic)
     cls = cls.reshape(-1)
     N = int(np.prod(dims))
     ndim = len(dims)
@@ -266,12 +266,13 @@ def _nx_backbone(dims, planes, flow_axis=0):
     for d in range(ndim):
         g = planes[d].reshape(-1)
         n = list(ext)
-        n[d] -= 1
+        if d not in periodic:
+            n[d] -= 1
         idx = np.arange(int(np.prod(n)))
         c = [idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1])]
         i = c[0] + ext[0] * (c[1] + ext[1] * c[2])
-        step = [1, ext[0], ext[0] * ext[1]][d]
-        j = i + step
+        c[d] = (c[d] + 1) % ext[d]
+        j = c[0] + ext[0] * (c[1] + ext[1] * c[2])
         ok = (g > 0) & keep[i] & keep[j] & ~(face[i] & face[j])
         G.add_edges_from(zip(i[ok].tolist(), j[ok].tolist()))
     G.add_edges_from([("S", "A"), ("A", "B"), ("B", "S")])
@@ -349,3 +350,114 @@ def test_backbone_stripping_is_exact():
         touch = (planes[d] > 0) & (dead[tuple(lo)] | dead[tuple(hi)])
         drop = np.abs(full.P[tuple(lo)] - full.P[tuple(hi)])[touch]
         assert drop.max() < 1e-9
+
+
+# ---------------------------------------------------------------- periodic transverse boundaries
+# Sec. II allows the transverse faces to be periodic: the last layer of bonds
+# along a periodic axis joins the last node layer to the first.
+def _periodic_net(dims, periodic, p, seed):
+    gen = netgen.rng(9300 + seed)
+    planes = netgen.lognormal_iid(dims, gen, periodic=periodic)
+    return netgen.percolate(planes, p, gen)
+
+
+@pytest.mark.parametrize("dims,f,per", [((9, 7), 0, (1,)), ((7, 9), 1, (0,)),
+                                         ((5, 6, 7), 0, (1, 2)), ((5, 6, 7), 2, (0, 1)),
+                                         ((6, 3, 4), 0, (1,))])
+def test_periodic_uniform_closed_form(dims, f, per):
+    """Uniform g with periodic transverse axes: the wrap bonds join nodes at
+    the same pressure, so P stays linear and G = g S / R as without them."""
+    g = 1.5
+    r = oracle.solve(dims, netgen.uniform(dims, g, periodic=per), flow_axis=f,
+                     p_in=2.0, p_out=-2.0, periodic=per)
+    R = dims[f] - 1
+    S = int(np.prod(dims)) // dims[f]
+    assert rel(r.g_eff, g * S / R) < 1e-12
+    xs, ys, zs, _ = ind.node_coords(dims)
+    c = [xs, ys, zs][f]
+    np.testing.assert_allclose(r.P.reshape(-1), 2.0 - 4.0 * c / R, rtol=0, atol=1e-12)
+
+
+def test_periodic_wrap_only_path():
+    """A 3x4 network whose only inlet-outlet path runs through a wrap bond:
+    inlet (0,0) -a- (1,0) -w- (1,3) -b- (2,3) outlet, the middle bond being
+    the one from row 3 back to row 0.  G is the series value 1/(1/a+1/w+1/b);
+    without periodic boundaries nothing spans."""
+    dims = (3, 4)
+    a, w, b = 2.0, 0.5, 4.0
+    gx = np.zeros((4, 2))
+    gy = np.zeros((4, 3))
+    gx[0, 0] = a
+    gx[3, 1] = b
+    gy[3, 1] = w
+    r = oracle.solve(dims, [gx, gy], p_in=1.0, p_out=0.0, periodic=(1,))
+    want = 1.0 / (1.0 / a + 1.0 / w + 1.0 / b)
+    assert rel(r.g_eff, want) < 1e-13
+    # the two interior pressures of the series chain
+    assert abs(r.P[0, 1] - (1.0 - want / a)) < 1e-13
+    assert abs(r.P[3, 1] - want / b) < 1e-13
+    closed = oracle.solve(dims, [gx, gy[:3]], p_in=1.0, p_out=0.0)
+    assert closed.g_eff == 0.0
+
+
+@pytest.mark.parametrize("dims,f,per,p", [((6, 5), 0, (1,), 1.0), ((5, 7), 1, (0,), 0.7),
+                                           ((4, 3, 5), 0, (1, 2), 1.0), ((4, 3, 5), 2, (0,), 0.6),
+                                           ((9, 8), 0, (1,), 0.55), ((5, 4, 4), 1, (0, 2), 0.5)])
+def test_periodic_dense_direct_solve(dims, f, per, p):
+    """CG with wrap bonds equals a dense solve of the incidence-matrix form
+    built from the bond list with the wrap bonds in it."""
+    planes = _periodic_net(dims, per, p, len(dims) * 10 + f)
+    r = oracle.solve(dims, planes, flow_axis=f, p_in=2.0, p_out=0.5, periodic=per)
+    P, qin, qout = ind.dense_solve(dims, planes, f, 2.0, 0.5, periodic=per)
+    np.testing.assert_allclose(r.P.reshape(-1), P, rtol=0, atol=1e-11)
+    assert abs(r.q_in - qin) <= 1e-11 * max(1.0, abs(qin))
+    assert abs(r.q_out - qout) <= 1e-11 * max(1.0, abs(qout))
+
+
+@pytest.mark.parametrize("dims,f,per,p,seed", [((7, 6), 0, (1,), 0.5, 1), ((6, 7), 1, (0,), 0.45, 2),
+                                                ((5, 4, 6), 0, (1, 2), 0.3, 3),
+                                                ((4, 5, 3), 2, (0, 1), 0.35, 4)])
+def test_periodic_labels_bruteforce_bfs(dims, f, per, p, seed):
+    planes = _periodic_net(dims, per, p, 20 + seed)
+    lab, cls = oracle.labels(dims, planes, flow_axis=f, periodic=per)
+    blab, bcls = ind.bfs_labels(dims, planes, f, periodic=per)
+    np.testing.assert_array_equal(lab.reshape(-1), blab)
+    np.testing.assert_array_equal(cls.reshape(-1), bcls)
+
+
+@pytest.mark.parametrize("dims,f,per,shift", [((12, 10), 0, (1,), (0, 3)),
+                                               ((8, 7, 6), 2, (0, 1), (5, 2, 0)),
+                                               ((7, 9, 5), 0, (1, 2), (0, 4, 2))])
+def test_periodic_cyclic_shift_invariance(dims, f, per, shift):
+    """Rolling a periodic network along its periodic axes (nodes and bonds
+    alike) rolls P the same way and leaves G unchanged; without the wrap
+    bonds this fails, so it checks that they join the right nodes."""
+    planes = _periodic_net(dims, per, 0.8, 40 + f)
+    axes = tuple(len(dims) - 1 - d for d in range(len(dims)))
+    sh = tuple(shift[d] for d in range(len(dims)))
+    rolled = [np.roll(g, sh, axis=axes) for g in planes]
+    r0 = oracle.solve(dims, planes, flow_axis=f, periodic=per, tol=1e-14)
+    r1 = oracle.solve(dims, rolled, flow_axis=f, periodic=per, tol=1e-14)
+    assert rel(r1.g_eff, r0.g_eff) < 1e-11
+    np.testing.assert_allclose(r1.P, np.roll(r0.P, sh, axis=axes), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("dims,f,per,p,seed", [((14, 11), 0, (1,), 0.6, 1),
+                                                ((9, 8, 7), 0, (1, 2), 0.34, 2),
+                                                ((8, 9, 10), 2, (0, 1), 0.33, 3)])
+def test_periodic_backbone_equals_kcore(dims, f, per, p, seed):
+    planes = _periodic_net(dims, per, p, 60 + seed)
+    bb = oracle.backbone(dims, planes, f, periodic=per).reshape(-1)
+    np.testing.assert_array_equal(bb, _nx_backbone(dims, planes, f, periodic=per))
+
+
+def test_periodic_invalid_inputs_rejected():
+    dims = (8, 6)
+    with pytest.raises(ValueError):     # the flow axis cannot be periodic
+        oracle.solve(dims, netgen.uniform(dims, periodic=(0,)), periodic=(0,))
+    with pytest.raises(ValueError):     # plane with the non-periodic shape
+        oracle.solve(dims, netgen.uniform(dims), periodic=(1,))
+    with pytest.raises(ValueError):     # a periodic axis needs three layers
+        oracle.solve((8, 2), netgen.uniform((8, 2), periodic=(1,)), periodic=(1,))
+    with pytest.raises(ValueError):     # axis beyond ndim
+        oracle.solve(dims, netgen.uniform(dims), periodic=(2,))
