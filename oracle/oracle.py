@@ -172,3 +172,27 @@ def solve(dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, tol=1e-13, max_iter=10
 
 def max_threads() -> int:
     return int(_load().or_max_threads())
+
+
+def close_smallest(planes, q):
+    """Correlated percolation by sorted removal (Sec. VI.B): of all M bonds
+    (the planes concatenated in plane order, each in its own x-fastest
+    order), close (set to 0) the floor(q M) with the smallest conductance;
+    equal conductances are taken in that position order.  A stable sort is
+    the whole method here.  Returns new planes of the input dtype."""
+    if not (0.0 <= q <= 1.0):
+        raise ValueError("q must lie in [0, 1]")
+    flat = np.concatenate([np.asarray(g).reshape(-1) for g in planes]).astype(np.float64)
+    if not np.all(np.isfinite(flat)) or np.any(flat < 0):
+        raise ValueError("conductances must be finite and non-negative")
+    k = int(np.floor(q * flat.size))
+    order = np.argsort(flat, kind="stable")
+    closed = np.zeros(flat.size, bool)
+    closed[order[:k]] = True
+    out, o = [], 0
+    for g in planes:
+        g = np.asarray(g)
+        c = closed[o:o + g.size].reshape(g.shape)
+        out.append(np.where(c, g.dtype.type(0), g))
+        o += g.size
+    return out

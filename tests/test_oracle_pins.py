@@ -461,3 +461,54 @@ def test_periodic_invalid_inputs_rejected():
         oracle.solve((8, 2), netgen.uniform((8, 2), periodic=(1,)), periodic=(1,))
     with pytest.raises(ValueError):     # axis beyond ndim
         oracle.solve(dims, netgen.uniform(dims), periodic=(2,))
+
+
+# ---------------------------------------------------------------- sorted removal (Sec. VI.B)
+def _brute_close(planes, q):
+    """Tiny-input brute force: rank every bond by (value, plane, index) with
+    Python's sort and close the first floor(q M)."""
+    items = []
+    for d, g in enumerate(planes):
+        for i, v in enumerate(np.asarray(g, dtype=np.float64).reshape(-1).tolist()):
+            items.append((v, d, i))
+    k = int(np.floor(q * len(items)))
+    shut = {(d, i) for _, d, i in sorted(items)[:k]}
+    out = []
+    for d, g in enumerate(planes):
+        f = np.asarray(g).reshape(-1).copy()
+        for i in range(f.size):
+            if (d, i) in shut:
+                f[i] = 0
+        out.append(f.reshape(np.shape(g)))
+    return out
+
+
+@pytest.mark.parametrize("dims,q,levels,seed", [((5, 4), 0.5, 0, 1), ((6, 5, 4), 0.3, 3, 2),
+                                                 ((7, 3), 1.0, 2, 3), ((4, 4, 4), 0.0, 0, 4),
+                                                 ((9, 8), 0.77, 4, 5)])
+def test_close_smallest_bruteforce(dims, q, levels, seed):
+    """Equal values (few levels) and zeros test the position order of ties."""
+    gen = netgen.rng(9400 + seed)
+    planes = netgen.lognormal_iid(dims, gen)
+    if levels:
+        planes = [np.floor(g * levels) / levels for g in planes]
+    got = oracle.close_smallest(planes, q)
+    want = _brute_close(planes, q)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_close_smallest_invariants():
+    gen = netgen.rng(9450)
+    dims = (30, 20, 10)
+    planes = [g.astype(np.float32) for g in netgen.lognormal_iid(dims, gen)]
+    M = sum(g.size for g in planes)
+    for q in (0.1, 0.5, 0.9):
+        out = oracle.close_smallest(planes, q)
+        closed = np.concatenate([(o == 0).reshape(-1) for o in out])
+        vals = np.concatenate([g.reshape(-1) for g in planes])
+        assert closed.sum() == int(np.floor(q * M))   # all values positive
+        assert vals[closed].max() <= vals[~closed].min()
+        assert all(o.dtype == np.float32 for o in out)
+    with pytest.raises(ValueError):
+        oracle.close_smallest(planes, 1.5)
