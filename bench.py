@@ -44,7 +44,7 @@ def args_():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fbm2048",
-                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso"],
+                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic"],
                     help="fbm2048: the headline 2048^2 solve; perc3d: 256^3 percolation; batch: "
                          "512 networks in one batched solve; serve: the request queue; aniso: "
                          "K_x/K_y of anisotropic FBM networks (both axes batched)")
@@ -618,6 +618,68 @@ def run_aniso(a):
     print(json.dumps(line), flush=True)
 
 
+def run_periodic(a):
+    """The 2048^2 FBM network of the headline (H = 0.7, sigma = 1.5) with the
+    paper's own boundaries (Sec. II): pressure drop along x, periodic y.  The
+    network is resident; each step is one mixed solve (L2 flushed before it).
+    Periodic networks take the compacted solve, whose neighbour table holds
+    the wrap bonds; the same network with no-flow y is the headline."""
+    import torch
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    dims, planes = netgen.workload_fbm2d(periodic=(1,))
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    net = ns.Network(dims, planes, periodic=(1,))
+
+    def steps(precision, k, w):
+        opts = ns.make_opts(precision=precision, tol_rel=TOL_REL, stream=stream.cuda_stream)
+        for _ in range(w):
+            net.solve(opts)
+        ms, res = [], []
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = net.solve(opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            res.append(r)
+        return ms, res
+
+    (ms, res), clocks = _clocked(lambda: steps(ns.NET_MIXED, a.steps, a.warmup))
+    ms64, res64 = steps(ns.NET_FP64, max(1, a.fp64_steps), 1)
+    net.close()
+    r0 = res[-1]
+    b_alg = 40 * r0.n_solved  # 32 + 4d bytes per unknown and iteration, d = 2
+    it_s = r0.inner_ms / 1e3 / max(1, r0.inner_iters)
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    line = {"metric": METRIC, "workload": "periodic", "value": len(ms) / (sum(ms) / 1e3),
+            "unit": "solves/s", "ms_per_step": statistics.mean(ms), "steps": len(ms),
+            "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "2D 2048^2 FBM network H=0.7 sigma=1.5, flow along x, periodic y "
+                                   "(network resident, L2 flushed between steps)",
+                       "n_solved": r0.n_solved, "tol_rel": TOL_REL},
+            "accuracy": {"g_eff": r0.g_eff, "g_eff_fp64": res64[-1].g_eff,
+                         "rel_mixed_vs_fp64": abs(r0.g_eff - res64[-1].g_eff) / max(abs(res64[-1].g_eff), 1e-300),
+                         "g_eff_err_estimate": r0.g_eff_err, "outer_iters": r0.outer_iters,
+                         "inner_iters": r0.inner_iters, "fp64_fallback": r0.fp64_fallback},
+            "fp64_cg": {"value": len(ms64) / (sum(ms64) / 1e3), "unit": "solves/s",
+                        "ms_per_step": statistics.mean(ms64), "inner_iters": res64[-1].inner_iters},
+            "inner": {"kernel": "compact_cg_kernel (listed unknowns, wrap bonds in the table)",
+                      "us_per_iteration": it_s * 1e6, "algorithmic_gbs": b_alg / it_s / 1e9,
+                      "frac": b_alg / it_s / 1e9 / peak,
+                      "bytes_note": "algorithmic = 40 B x unknowns per CG iteration; peak = measured copy"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.profile_solve:
@@ -626,9 +688,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if a.workload in ("perc3d", "serve", "aniso") and a.impl == "ours":
+    if a.workload in ("perc3d", "serve", "aniso", "periodic") and a.impl == "ours":
         if rank == 0:
-            {"perc3d": run_perc3d, "serve": run_serve, "aniso": run_aniso}[a.workload](a)
+            {"perc3d": run_perc3d, "serve": run_serve, "aniso": run_aniso,
+             "periodic": run_periodic}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)

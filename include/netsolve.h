@@ -8,8 +8,9 @@
  *   Sec. II   each bond ij carries q_ij = g_ij (P_j - P_i);
  *   Eq. 3     mass balance sum_j q_ij = 0 at every interior node: G P = b;
  *   Sec. II   a fixed pressure drop along one axis: the face x_f = 0 is held
- *             at p_in and the face x_f = n_f - 1 at p_out (here the transverse
- *             boundaries are no-flow);
+ *             at p_in and the face x_f = n_f - 1 at p_out; each transverse
+ *             boundary is no-flow (the default) or periodic, the paper's
+ *             stated choice (periodic_mask; y and z only);
  *   Eq. 4     K = (Q / S)(mu L / dP), with Q the total flow through the inlet
  *             face, L = n_f - 1, S = product of the transverse node counts
  *             and mu = 1 (lattice units);
@@ -27,8 +28,9 @@
  * Layout of every node array: node (x, y, z) has linear index
  * x + nx * (y + ny * z), x fastest.  Bond plane d (0 = x, 1 = y, 2 = z) holds
  * the bond from node c to node c + e_d; its extents are the node extents with
- * n_d reduced by one, indexed the same way (x fastest).  A plane of extent 0
- * (e.g. ny = 1) may be NULL.
+ * n_d reduced by one, indexed the same way (x fastest).  Along a periodic
+ * axis n_d is not reduced: the last layer holds the bonds from layer n_d - 1
+ * back to layer 0.  A plane of extent 0 (e.g. ny = 1) may be NULL.
  *
  * Errors: every call returns a net_status; nothing aborts or throws across
  * this boundary.  net_last_error() gives a thread-local message for the last
@@ -95,7 +97,13 @@ typedef struct {
     int64_t n[3];            /* node extents (nx, ny, nz); n[2] = 1 in 2D */
     int flow_axis;           /* axis of the pressure drop, 0 <= flow_axis < ndim;
                                 n[flow_axis] >= 3 */
-    unsigned periodic_mask;  /* must be 0 (no-flow transverse boundaries) */
+    unsigned periodic_mask;  /* bit d set: axis d is periodic (Sec. II); only
+                                y (bit 1) and z (bit 2), never the flow axis,
+                                each with n[d] >= 3.  0: no-flow boundaries.
+                                Periodic networks are solved by net_solve
+                                (the compacted CG); net_solve_batch, netq_*,
+                                net_autotune and net_labels_noalloc reject
+                                them with NET_EINVAL. */
     double p_in, p_out;      /* face pressures, finite, p_in != p_out */
     int bond_dtype;          /* NET_F64 or NET_F32 */
     int on_device;           /* 1: bond pointers are device pointers on the
@@ -172,7 +180,8 @@ void net_opts_default(net_opts *opts);
  *   out    receives the handle; the library owns its device state until
  *          net_destroy.
  * Errors: NET_EINVAL for ndim not 2/3, an extent < 1, n_f < 3, more than
- * 2^31 - 1 padded nodes, periodic_mask != 0, non-finite or equal pressures,
+ * 2^31 - 1 padded nodes, a periodic_mask with bit 0, the flow axis or an
+ * axis beyond ndim set, or a periodic extent < 3, non-finite or equal pressures,
  * or a conductance that is negative, NaN or infinite (checked on the
  * device); NET_ENOMEM / NET_ECUDA otherwise.  A network without a spanning
  * cluster is valid and solves to g_eff = 0.  The call returns after the
@@ -258,6 +267,27 @@ net_status net_destroy(net_t *net);
 #define NET_NOALLOC_MAX_NODES (1LL << 20)
 net_status net_labels_noalloc(const net_desc *desc, const void *const g[3], int32_t *label,
                               uint8_t *cls);
+
+/*
+ * Correlated percolation by sorted removal (Sec. VI.B): of the M bonds of
+ * the planes g[0..ndim-1] (taken in plane order, each x fastest), close (set
+ * to 0) the floor(q * M) of smallest conductance, q * M computed in double.
+ * Equal conductances close in that position order, so the closed set is
+ * unique; 0 and -0 count as equal.  Unlike i.i.d. percolation this keeps the
+ * field's correlations in the open bonds.
+ *   desc   as for net_create (its dims, bond_dtype and periodic_mask fix the
+ *          plane sizes); desc->on_device must be 1; the work runs on
+ *          desc->stream (NULL = the default stream) and the call returns
+ *          after it has finished.
+ *   g[d]   device bond planes, modified in place; the caller keeps ownership.
+ *   q      fraction to close, 0 <= q <= 1.
+ * Device scratch (a few KB, plus 12 bytes per 4096 bonds when equal
+ * conductances straddle the cut) is allocated and freed on the stream.
+ * Errors: NET_EINVAL for a bad descriptor, q outside [0, 1], a NULL plane,
+ * or a negative, NaN or infinite conductance (then nothing is written);
+ * NET_ECUDA otherwise.
+ */
+net_status net_close_smallest(const net_desc *desc, void *const g[3], double q);
 
 /*
  * Solve `count` independent networks together.  Every sweep of the CG loop

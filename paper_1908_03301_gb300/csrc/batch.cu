@@ -435,11 +435,16 @@ NET_API net_status net_solve_batch(net_t *const *nets, int count, const net_opts
     if (count == 0) return NET_OK;
     int dev = 0;
     cudaGetDevice(&dev);
-    for (int i = 0; i < count; i++)
+    for (int i = 0; i < count; i++) {
         if (!nets[i] || nets[i]->device != dev) {
             set_error("net_solve_batch: network %d is NULL or on another device", i);
             return NET_EINVAL;
         }
+        if (nets[i]->g.per) {
+            set_error("net_solve_batch: network %d is periodic; solve it with net_solve", i);
+            return NET_EINVAL;
+        }
+    }
     net_opts o;
     net_opts_default(&o);
     if (opts) o = *opts;

@@ -117,7 +117,8 @@ __global__ void compact_index_kernel(Geom g, const uint8_t *__restrict__ cls,
 }
 
 // ELL row of every unknown.  In lattice order an unknown's +x neighbour, if
-// it is an unknown, is the next entry of the list, so x needs no index.
+// it is an unknown, is the next entry of the list, so x needs no index (x is
+// never periodic).  The y and z neighbours follow periodic boundaries.
 //   val[d][k]  (d < ndim, stride U + 1): scaled bond to the +e_d neighbour if
 //              that node is an unknown, else 0 (val[d][U] = 0);
 //   nbr[2(d-1)][k], nbr[2(d-1)+1][k]  (d >= 1, stride U): list index of the
@@ -133,15 +134,23 @@ __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ 
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = cidx[k];
+        // coordinates matter only across a periodic (y / z) boundary
+        int c[3] = {0, 0, 0};
+        if (g.per) {
+            const long long t = i - g.pad, r = t / g.px;
+            c[1] = (int)(r % g.ny);
+            c[2] = (int)(r / g.ny);
+        }
         for (int d = 0; d < g.ndim; d++) {
-            const long long s = g.stride(d);
+            const long long jp = d == 0 ? i + 1 : g.up(i, d, c[d]);
             const T gp = gs[d][i];
-            const int mp = cmap[i + s];
+            const int mp = cmap[jp];
             const bool lp = mp >= 0 && gp != T(0);
             val[(long long)d * (U + 1) + k] = lp ? gp : T(0);
             if (d == 0) continue;
-            const T gm = gs[d][i - s];
-            const int mm = cmap[i - s];
+            const long long jm = g.down(i, d, c[d]);
+            const T gm = gs[d][jm];
+            const int mm = cmap[jm];
             const bool lm = mm >= 0 && gm != T(0);
             nbr[(long long)(2 * (d - 1)) * U + k] = lp ? mp : (int)k;
             nbr[(long long)(2 * (d - 1) + 1) * U + k] = lm ? mm : ~(int)k;

@@ -7,7 +7,11 @@
 // `pad` zero elements precede and follow the grid (pad >= the largest
 // neighbour offset), so the stencil never indexes outside an allocation.
 // Bond plane d over the padded grid holds at idx(c) the conductance of the
-// bond c -> c + e_d, and 0 where that bond does not exist.
+// bond c -> c + e_d, and 0 where that bond does not exist.  Along a periodic
+// axis (y or z) the last layer's bonds lead back to layer 0; only the set-up
+// kernels, the FP64 residual pass and the compacted solve (whose neighbour
+// table holds the wrap) follow them, so periodic networks always take the
+// compacted solve.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -24,6 +28,7 @@ struct Geom {
     long long pad;   // zero elements before (and after) the grid
     long long len;   // pad + plane * nz + pad
     double p_in, p_out;
+    unsigned per;    // bit d: axis d is periodic (y or z, never the flow axis)
 
     __host__ __device__ long long idx(int x, int y, int z) const {
         return pad + x + (long long)px * (y + (long long)ny * z);
@@ -36,6 +41,18 @@ struct Geom {
     }
     __host__ __device__ int extent(int d) const {
         return d == 0 ? nx : (d == 1 ? ny : nz);
+    }
+    __host__ __device__ bool periodic(int d) const { return (per >> d) & 1u; }
+    // Neighbour of node i (coordinate cd along d) one step along +e_d / -e_d.
+    // Off a no-flow boundary this is i +- stride(d) as everywhere else (a
+    // ghost or pad node with zero bonds and vectors); across a periodic
+    // boundary it wraps to the opposite layer.
+    __host__ __device__ long long up(long long i, int d, int cd) const {
+        return (cd + 1 == extent(d) && periodic(d)) ? i - (long long)(extent(d) - 1) * stride(d)
+                                                    : i + stride(d);
+    }
+    __host__ __device__ long long down(long long i, int d, int cd) const {
+        return (cd == 0 && periodic(d)) ? i + (long long)(extent(d) - 1) * stride(d) : i - stride(d);
     }
 };
 

@@ -318,9 +318,20 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
         double rs = 0.0;
 #pragma unroll
         for (int d = 0; d < NDIM; d++) {
+            double gmv = (double)gp[d][i - g.stride(d)];
+            double xpv = sx[s0 + soff[d]], xmv = sx[s0 - soff[d]];
+            if (g.periodic(d)) {
+                // across a periodic boundary the neighbour is the opposite
+                // layer, outside this tile's halo: read it directly
+                const int cd = g.coord(d, cx, cy, cz);
+                if (cd + 1 == g.extent(d)) xpv = x[g.up(i, d, cd)];
+                if (cd == 0) {
+                    const long long jm = g.down(i, d, cd);
+                    xmv = x[jm];
+                    gmv = (double)gp[d][jm];
+                }
+            }
             const double gpv = (double)gp[d][i];
-            const double gmv = (double)gp[d][i - g.stride(d)];
-            const double xpv = sx[s0 + soff[d]], xmv = sx[s0 - soff[d]];
             rs += gpv * (xpv - xi) + gmv * (xmv - xi);
             en += gpv * (xi - xpv) * (xi - xpv);
         }

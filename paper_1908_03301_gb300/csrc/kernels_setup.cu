@@ -49,14 +49,15 @@ template <typename S, typename D>
 __global__ void pack_kernel(Geom g, int d, const S *__restrict__ src, D *__restrict__ dst,
                             unsigned int *bad) {
     const long long n = grid_nodes(g);
-    const int mx = g.nx - (d == 0), my = g.ny - (d == 1);
+    const int last = g.periodic(d) ? 0 : 1;  // a periodic plane has a bond per node
+    const int mx = g.nx - (d == 0) * last, my = g.ny - (d == 1) * last;
     for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n;
          t += (long long)gridDim.x * NT) {
         int x, y, z;
         unflatten(g, t, x, y, z);
         D v = D(0);
         const int c = g.coord(d, x, y, z);
-        if (x < g.nx && c < g.extent(d) - 1) {
+        if (x < g.nx && c < g.extent(d) - last) {
             S s = src[x + (long long)mx * (y + (long long)my * z)];
             if (!(s >= S(0)) || isinf((double)s)) atomicOr(bad, 1u);
             v = (D)s;
@@ -120,9 +121,10 @@ __global__ void lab_link(Geom g, const void *g0, const void *g1, const void *g2,
         for (int d = 0; d < g.ndim; d++) {
             if (!(bond_at(gp[d], f32, i) > 0.0)) continue;
             int c[3] = {x, y, z};
-            c[d] += 1;  // the bond exists, so the neighbour is inside the grid
+            // the bond exists, so the neighbour is inside the grid
+            c[d] = c[d] + 1 == g.extent(d) ? 0 : c[d] + 1;
             if (!interior(g, c[0], c[1], c[2])) continue;
-            uf_union(parent, (int)i, (int)(i + g.stride(d)));
+            uf_union(parent, (int)i, (int)g.idx(c[0], c[1], c[2]));
         }
     }
 }
@@ -196,9 +198,9 @@ __global__ void prune_round_kernel(Geom g, const void *g0, const void *g1, const
         int links = 0;
         long long last = -1;
         for (int d = 0; d < g.ndim; d++) {
-            const long long s = g.stride(d);
+            const int cd = g.coord(d, x, y, z);
             for (int side = 0; side < 2; side++) {
-                const long long j = side ? i - s : i + s;
+                const long long j = side ? g.down(i, d, cd) : g.up(i, d, cd);
                 if (!(bond_at(gp[d], f32, side ? j : i) > 0.0)) continue;
                 const uint8_t cj = cls[j];
                 const unsigned int pj = *(volatile const unsigned int *)&pr[j];
@@ -299,9 +301,10 @@ __global__ void build_system_kernel(Geom g, const void *g0, const void *g1, cons
             // are not part of it
             double D = 0.0;
             for (int d = 0; d < g.ndim; d++) {
-                const long long s = g.stride(d);
-                if (cls[i + s] != CLS_DANGLING) D += bond_at(gp[d], f32, i);
-                if (cls[i - s] != CLS_DANGLING) D += bond_at(gp[d], f32, i - s);
+                const int cd = g.coord(d, cx, cy, cz);
+                const long long jp = g.up(i, d, cd), jm = g.down(i, d, cd);
+                if (cls[jp] != CLS_DANGLING) D += bond_at(gp[d], f32, i);
+                if (cls[jm] != CLS_DANGLING) D += bond_at(gp[d], f32, jm);
             }
             dv = 1.0 / sqrt(D);
             double b = 0.0;
@@ -337,7 +340,7 @@ __global__ void build_scaled_kernel(Geom g, const void *g0, const void *g1, cons
         const long long i = g.idx(x, y, z);
         const double di = dis[i];
         for (int d = 0; d < g.ndim; d++) {
-            const double dj = dis[i + g.stride(d)];
+            const double dj = dis[g.up(i, d, g.coord(d, x, y, z))];
             const double gv = bond_at(gp[d], f32, i);
             sp[d][i] = (di > 0.0 && dj > 0.0) ? (T)(gv * di * dj) : T(0);
         }

@@ -200,6 +200,10 @@ NET_API net_status net_labels_noalloc(const net_desc *desc, const void *const g[
         netsolve::set_error("net_labels_noalloc: bond planes must be device pointers (on_device = 1)");
         return NET_EINVAL;
     }
+    if (G.per) {
+        netsolve::set_error("net_labels_noalloc: periodic networks are labelled by net_create");
+        return NET_EINVAL;
+    }
     Shape s{};
     s.ndim = desc->ndim;
     s.f = desc->flow_axis;

@@ -88,7 +88,18 @@ net_status make_geom(const net_desc *d, Geom *g) {
     if (d->ndim == 2 && d->n[2] != 1) { set_error("2D network needs n[2] == 1"); return NET_EINVAL; }
     if (d->flow_axis < 0 || d->flow_axis >= d->ndim) { set_error("flow_axis out of range"); return NET_EINVAL; }
     if (d->n[d->flow_axis] < 3) { set_error("need at least 3 nodes along the flow axis"); return NET_EINVAL; }
-    if (d->periodic_mask != 0) { set_error("periodic boundaries are not supported"); return NET_EINVAL; }
+    if (d->periodic_mask >> d->ndim) { set_error("periodic_mask names an axis beyond ndim"); return NET_EINVAL; }
+    if ((d->periodic_mask >> d->flow_axis) & 1u) { set_error("the flow axis cannot be periodic"); return NET_EINVAL; }
+    if (d->periodic_mask & 1u) {
+        // the compacted solve finds an x neighbour as the adjacent list entry
+        set_error("periodic x is not supported: put the flow along x, periodic y/z");
+        return NET_EINVAL;
+    }
+    for (int a = 1; a < d->ndim; a++)
+        if (((d->periodic_mask >> a) & 1u) && d->n[a] < 3) {
+            set_error("a periodic axis needs at least 3 nodes");
+            return NET_EINVAL;
+        }
     if (!std::isfinite(d->p_in) || !std::isfinite(d->p_out) || d->p_in == d->p_out) {
         set_error("face pressures must be finite and differ");
         return NET_EINVAL;
@@ -109,6 +120,7 @@ net_status make_geom(const net_desc *d, Geom *g) {
     G.len = G.pad + G.plane * G.nz + G.pad;
     G.p_in = d->p_in;
     G.p_out = d->p_out;
+    G.per = d->periodic_mask;
     if (G.len >= (1LL << 31)) { set_error("network too large (padded nodes >= 2^31)"); return NET_EINVAL; }
     *g = G;
     return NET_OK;
@@ -116,7 +128,7 @@ net_status make_geom(const net_desc *d, Geom *g) {
 
 long long plane_elems(const Geom &g, int d) {
     long long m[3] = {g.nx, g.ny, g.nz};
-    m[d] -= 1;
+    if (!g.periodic(d)) m[d] -= 1;  // a periodic plane has a bond per node
     return m[0] * m[1] * m[2];
 }
 
@@ -189,9 +201,11 @@ bool use_sweep_kernel() {
 // The compacted solve replaces the lattice kernels when the unknowns are a
 // small part of the lattice (its list traffic is about twice a lattice
 // sweep's per node): below 35 % of the lattice nodes, or always with
-// NETSOLVE_KERNEL=compact.
+// NETSOLVE_KERNEL=compact.  Periodic networks always take it: its neighbour
+// table holds the wrap bonds, the lattice stencils do not.
 bool use_compact_kernel(const net_t *n, int) {
     if (n->n_solved <= 0) return false;
+    if (n->g.per) return true;
     const char *e = getenv("NETSOLVE_KERNEL");
     if (e && strcmp(e, "compact") == 0) return true;
     if (e && *e) return false;
@@ -200,7 +214,7 @@ bool use_compact_kernel(const net_t *n, int) {
 }
 
 bool use_persist_kernel(const net_t *n, int f32) {
-    if (use_compact_kernel(n, f32)) return false;
+    if (use_compact_kernel(n, f32) || n->g.per) return false;
     const char *e = getenv("NETSOLVE_KERNEL");
     if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0 || strcmp(e, "compact") == 0)) return false;
     return persist_applies(n->g, f32);
@@ -769,7 +783,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
     if (use_compact_kernel(n, f32)) {
         s = ensure_compact(n, f32, st);
         if (s != NET_OK) return r->status = s;
-    } else if (!use_persist_kernel(n, f32)) {
+    } else if (!use_persist_kernel(n, f32) && !G.per) {
+        // (a periodic network without unknowns runs no inner solve)
         s = ensure_graph(n, f32, K);
         if (s != NET_OK) return r->status = s;
     }
@@ -908,7 +923,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             fallback = 1;
             s = ensure_precision(n, 0, st);
             if (s != NET_OK) return r->status = s;
-            if (!use_persist_kernel(n, 0) && !use_compact_kernel(n, 0)) {
+            if (!use_persist_kernel(n, 0) && !use_compact_kernel(n, 0) && !G.per) {
                 s = ensure_graph(n, 0, K);
                 if (s != NET_OK) return r->status = s;
             }
@@ -991,6 +1006,10 @@ NET_API net_status net_autotune(net_t *const *nets, int count, const net_opts *o
         }
         if (nets[i]->g.ndim != nets[0]->g.ndim) {
             set_error("net_autotune: networks mix 2D and 3D");
+            return NET_EINVAL;
+        }
+        if (nets[i]->g.per) {
+            set_error("net_autotune: network %d is periodic (it takes the compacted solve)", i);
             return NET_EINVAL;
         }
         v.push_back(nets[i]);

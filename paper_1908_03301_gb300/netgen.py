@@ -55,12 +55,16 @@ def n_bonds(dims, periodic=()):
     return [int(np.prod(plane_shape(dims, d, periodic))) for d in range(len(dims))]
 
 
-def _node_to_bonds(field, dims):
-    """Bond value = mean of the two end-node values, for each direction."""
+def _node_to_bonds(field, dims, periodic=()):
+    """Bond value = mean of the two end-node values, for each direction
+    (along a periodic axis the last bond joins the last and first layers)."""
     ndim = len(dims)
     out = []
     for d in range(ndim):
         ax = ndim - 1 - d  # numpy axis of lattice direction d
+        if d in periodic:
+            out.append(0.5 * (field + np.roll(field, -1, axis=ax)))
+            continue
         lo = [slice(None)] * ndim
         hi = [slice(None)] * ndim
         lo[ax] = slice(0, -1)
@@ -153,10 +157,11 @@ def fbm_aniso_bonds(dims, hurst, beta_x, beta_y, sigma, gen):
     return [np.exp(sigma * b) for b in _node_to_bonds(B, dims)]
 
 
-def fbm_bonds(dims, hurst, sigma, gen):
-    """Correlated conductances g = exp(sigma * B_b), B an FBM on the nodes."""
+def fbm_bonds(dims, hurst, sigma, gen, periodic=()):
+    """Correlated conductances g = exp(sigma * B_b), B an FBM on the nodes
+    (spectral synthesis makes B periodic, so wrap bonds fit it)."""
     B = fbm_field(node_shape(dims), hurst, gen)
-    return [np.exp(sigma * b) for b in _node_to_bonds(B, dims)]
+    return [np.exp(sigma * b) for b in _node_to_bonds(B, dims, periodic)]
 
 
 def fbm_stratified_bonds(dims, hurst, sigma, gen, noise=0.1):
@@ -217,13 +222,14 @@ def workload_small(variant="random", seed=None):
     raise ValueError(variant)
 
 
-def workload_fbm2d(n=2048, variant="isotropic", seed=None, hurst=0.7, sigma=1.5):
+def workload_fbm2d(n=2048, variant="isotropic", seed=None, hurst=0.7, sigma=1.5, periodic=()):
     """2D FBM network, H = 0.7, sigma = 1.5 (isotropic), or a stratified
-    version (1D FBM along y plus 10 % i.i.d. noise), or stratified without noise."""
+    version (1D FBM along y plus 10 % i.i.d. noise), or stratified without noise.
+    periodic=(1,) (isotropic only) adds the wrap bonds of a periodic y axis."""
     dims = (n, n)
     gen = rng(SEED_BASE + 1 if seed is None else seed)
     if variant == "isotropic":
-        return dims, fbm_bonds(dims, hurst, sigma, gen)
+        return dims, fbm_bonds(dims, hurst, sigma, gen, periodic)
     if variant == "stratified":
         return dims, fbm_stratified_bonds(dims, hurst, sigma, gen, noise=0.1)
     if variant == "stratified_exact":

@@ -63,7 +63,7 @@ EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_p
            "net_get_labels", "net_destroy", "net_solve_batch", "netq_create", "netq_submit",
            "netq_poll", "netq_wait", "netq_cancel", "netq_stats", "netq_destroy",
            "net_last_error", "net_labels_noalloc", "net_autotune", "net_tune_clear",
-           "net_get_backbone"]
+           "net_get_backbone", "net_close_smallest"]
 
 _lib = None
 
@@ -101,6 +101,8 @@ def lib(build_if_missing: bool = False):
     L.net_last_error.restype = C.c_char_p
     L.net_labels_noalloc.argtypes = [P(net_desc), P(vp), vp, vp]
     L.net_labels_noalloc.restype = C.c_int
+    L.net_close_smallest.argtypes = [P(net_desc), P(vp), C.c_double]
+    L.net_close_smallest.restype = C.c_int
     L.net_autotune.argtypes = [P(vp), C.c_int, P(net_opts), P(net_tune)]
     L.net_autotune.restype = C.c_int
     L.net_tune_clear.argtypes = []
@@ -173,11 +175,27 @@ def _is_torch(a):
     return type(a).__module__.startswith("torch")
 
 
+def periodic_mask(periodic):
+    """Axes (iterable of 0/1/2) -> net_desc.periodic_mask."""
+    m = 0
+    for a in periodic:
+        m |= 1 << int(a)
+    return m
+
+
+def plane_elems(dims, d, periodic=()):
+    """Number of bonds in plane d (the last layer wraps along a periodic axis)."""
+    n = [int(v) for v in dims]
+    if d not in periodic:
+        n[d] -= 1
+    return int(np.prod(n))
+
+
 def make_desc(dims, flow_axis=0, p_in=1.0, p_out=0.0, bond_dtype=NET_F64, on_device=0,
-              stream=None) -> net_desc:
+              stream=None, periodic=()) -> net_desc:
     n = list(int(v) for v in dims) + [1] * (3 - len(dims))
-    return net_desc(len(dims), (C.c_int64 * 3)(*n), int(flow_axis), 0, float(p_in),
-                    float(p_out), int(bond_dtype), int(on_device), stream)
+    return net_desc(len(dims), (C.c_int64 * 3)(*n), int(flow_axis), periodic_mask(periodic),
+                    float(p_in), float(p_out), int(bond_dtype), int(on_device), stream)
 
 
 def marshal_planes(planes, ndim):
@@ -240,12 +258,17 @@ class Result:
 class Network:
     """One resident network (net_create ... net_destroy)."""
 
-    def __init__(self, dims, planes, flow_axis=0, p_in=1.0, p_out=0.0):
+    def __init__(self, dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, periodic=()):
         L = lib()
         self.dims = tuple(int(v) for v in dims)
         self.N = int(np.prod(self.dims))
+        for d in range(len(self.dims)):
+            size = planes[d].numel() if _is_torch(planes[d]) else np.size(planes[d])
+            if size != plane_elems(self.dims, d, periodic):
+                raise ValueError(f"bond plane {d} has {size} entries, expected "
+                                 f"{plane_elems(self.dims, d, periodic)}")
         keep, ptrs, bdt, dev, stream = marshal_planes(planes, len(dims))
-        desc = make_desc(dims, flow_axis, p_in, p_out, bdt, dev, stream)
+        desc = make_desc(dims, flow_axis, p_in, p_out, bdt, dev, stream, periodic)
         h = C.c_void_p()
         _check(L.net_create(C.byref(desc), ptrs, C.byref(h)), "net_create")
         self.h = h
@@ -314,6 +337,22 @@ class Network:
 
     def __exit__(self, *a):
         self.close()
+
+
+def close_smallest(dims, planes, q, periodic=(), flow_axis=0):
+    """net_close_smallest: close the floor(q M) weakest bonds of torch CUDA
+    planes in place (Sec. VI.B sorted removal); returns the planes."""
+    if not (_is_torch(planes[0]) and planes[0].is_cuda):
+        raise TypeError("close_smallest takes torch CUDA bond planes")
+    for d in range(len(dims)):
+        if not planes[d].is_contiguous():
+            raise ValueError("bond planes must be contiguous (they are modified in place)")
+        if planes[d].numel() != plane_elems(dims, d, periodic):
+            raise ValueError(f"bond plane {d} has {planes[d].numel()} entries")
+    keep, ptrs, bdt, dev, stream = marshal_planes(planes, len(dims))
+    desc = make_desc(dims, flow_axis, 1.0, 0.0, bdt, 1, stream, periodic)
+    _check(lib().net_close_smallest(C.byref(desc), ptrs, float(q)), "net_close_smallest")
+    return planes
 
 
 def solve_batch(networks, opts: net_opts | None = None, check=True):

@@ -55,9 +55,13 @@ def test_host_side_validation_without_gpu(so):
         d = ns.make_desc(dims, flow_axis=fa)
         assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
         assert L.net_last_error()
-    d = ns.make_desc((8, 8))
-    d.periodic_mask = 1
-    assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
+    # periodic boundaries: only y / z, never the flow axis, extent >= 3,
+    # no axis beyond ndim
+    for dims, fa, per in [((8, 8), 0, (0,)), ((8, 8), 1, (1,)), ((8, 8), 0, (2,)),
+                          ((8, 2), 0, (1,)), ((6, 6, 6), 2, (2,)), ((6, 6, 2), 0, (1, 2))]:
+        d = ns.make_desc(dims, flow_axis=fa, periodic=per)
+        assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL, (dims, fa, per)
+        assert L.net_last_error()
     d = ns.make_desc((8, 8), p_in=1.0, p_out=1.0)
     assert L.net_create(ctypes.byref(d), ptrs, ctypes.byref(h)) == ns.NET_EINVAL
     assert L.net_solve(None, None, None) == ns.NET_EINVAL
@@ -97,3 +101,16 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(val) == expect, (cname, field, int(val), expect)
         seen += 1
     assert seen == sum(len(p._fields_) + 1 for p in structs.values())
+
+
+def test_periodic_plane_sizes_checked_by_binding(so):
+    """A periodic axis has one bond per node along it; the binding refuses
+    planes of the no-flow size before calling the library."""
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    assert ns.plane_elems((8, 6), 1, periodic=(1,)) == 48
+    assert ns.plane_elems((8, 6), 1) == 40
+    assert ns.periodic_mask((1, 2)) == 6
+    with pytest.raises(ValueError):
+        ns.Network((8, 6), netgen.uniform((8, 6)), periodic=(1,))
