@@ -44,7 +44,7 @@ def args_():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fbm2048",
-                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic"],
+                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic", "corrperc"],
                     help="fbm2048: the headline 2048^2 solve; perc3d: 256^3 percolation; batch: "
                          "512 networks in one batched solve; serve: the request queue; aniso: "
                          "K_x/K_y of anisotropic FBM networks (both axes batched)")
@@ -680,6 +680,62 @@ def run_periodic(a):
     print(json.dumps(line), flush=True)
 
 
+def run_corrperc(a):
+    """Correlated percolation by sorted removal (Sec. VI.B, Fig. 9): a
+    1900^2 (3.6 M node) FBM network (H = 0.7, sigma = 1.5); for each q the
+    fraction q of weakest bonds is closed on the device (net_close_smallest),
+    then the network is created and solved.  q approaches q_c = 1/2, where
+    the solve slows down (critical slowing down).  Reports, per q, the
+    removal time and its HBM rate, the solve time and iterations."""
+    import torch
+
+    from paper_1908_03301_gb300 import netgen
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    dims = (1900, 1900)
+    gen = netgen.rng(netgen.SEED_BASE + 6)
+    host = netgen.fbm_bonds(dims, 0.7, 1.5, gen)
+    dev = torch.device("cuda", 0)
+    base = [torch.from_numpy(g).to(dev) for g in host]
+    stream = torch.cuda.current_stream(dev)
+    M = sum(g.numel() for g in base)
+    cells, solve_ms = [], []
+    for q in (0.2, 0.4, 0.45, 0.48):
+        rm, sv, res = [], [], None
+        for it in range(a.warmup + a.steps):
+            planes = [g.clone() for g in base]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            ns.close_smallest(dims, planes, q)
+            e[1].record(stream)
+            with ns.Network(dims, planes) as net:
+                r = net.solve(ns.make_opts(tol_rel=TOL_REL, stream=stream.cuda_stream))
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            if it >= a.warmup:
+                rm.append(e[0].elapsed_time(e[1]))
+                sv.append(e[1].elapsed_time(e[2]))
+                res = r
+        # 8 histogram passes over the FP64 bonds, one closing pass (read +
+        # write of the closed ones): the algorithmic bytes of one removal
+        b_rm = 9 * 8 * M + 8 * int(q * M)
+        cells.append({"q": q, "removal_ms": statistics.mean(rm),
+                      "removal_gbs": b_rm / (statistics.mean(rm) / 1e3) / 1e9,
+                      "create_and_solve_ms": statistics.mean(sv), "g_eff": res.g_eff,
+                      "n_active": res.n_active, "n_solved": res.n_solved,
+                      "inner_iters": res.inner_iters, "status": res.status})
+        solve_ms += [x + y for x, y in zip(rm, sv)]
+    line = {"metric": METRIC, "workload": "corrperc", "value": len(solve_ms) / (sum(solve_ms) / 1e3),
+            "unit": "solves/s", "steps": a.steps, "warmup": a.warmup, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "2D 1900^2 FBM network H=0.7 sigma=1.5, the weakest fraction q of "
+                                   "bonds closed on the device, then created and solved; q in "
+                                   "{0.2, 0.4, 0.45, 0.48}", "bonds": M, "tol_rel": TOL_REL},
+            "cells": cells}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.profile_solve:
@@ -688,10 +744,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if a.workload in ("perc3d", "serve", "aniso", "periodic") and a.impl == "ours":
+    if a.workload in ("perc3d", "serve", "aniso", "periodic", "corrperc") and a.impl == "ours":
         if rank == 0:
             {"perc3d": run_perc3d, "serve": run_serve, "aniso": run_aniso,
-             "periodic": run_periodic}[a.workload](a)
+             "periodic": run_periodic, "corrperc": run_corrperc}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)
