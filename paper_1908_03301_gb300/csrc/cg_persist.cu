@@ -99,14 +99,16 @@ __device__ __forceinline__ float *hb_row(const PersistArgs &a, int par, int cta,
 // vectors y, r, p, q are read and written every iteration (67 MB at 2048^2):
 // they are loaded and stored with an evict-last L2 policy, which keeps them in
 // the persisting part of L2 that the host sets aside for the solve; the bond
-// planes (read only) stream.
+// planes (read only) stream.  With a periodic y axis the bond row below row 0
+// is the wrap row ny-1.
 __device__ __forceinline__ void issue_row_stage(unsigned char *smem, uint64_t *full, int b, int t,
                                                 int row0, int row1, int px, bool first,
                                                 const PersistArgs &a, int lane, uint64_t pol) {
     const uint32_t rb = (uint32_t)px * 4u;
-    const int me = row0 + t + 1, mt = row0 + t;
-    const int nl = me < row1 ? (first ? 1 : 4) : 0;  // r [q p y] of row me
-    const int nb = mt >= 0 ? (t >= 0 ? 2 : 1) : 0;   // [gx] gy of row mt
+    const bool wrap = a.g.periodic(1);
+    const int me = row0 + t + 1, mt = row0 + t >= 0 ? row0 + t : a.g.ny - 1;
+    const int nl = me < row1 ? (first ? 1 : 4) : 0;                   // r [q p y] of row me
+    const int nb = (row0 + t >= 0 || wrap) ? (t >= 0 ? 2 : 1) : 0;  // [gx] gy of row mt
     if (lane == 0) mbar_arrive_expect_tx(&full[b], (uint32_t)(nl + nb) * rb);
     __syncwarp();
     const long long base = a.g.pad;
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
 
     const int G = gridDim.x, c = blockIdx.x;
     const int px = a.g.px, ny = a.g.ny;
+    const bool wrap = a.g.periodic(1);  // periodic y: row ny-1 joins row 0
     const int row0 = (int)((long long)c * ny / G), row1 = (int)((long long)(c + 1) * ny / G);
     const int n = row1 - row0;  // >= 1
     const int steps = n + 1;    // row stages per sweep: t = -1 .. n-1
@@ -191,17 +194,21 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             // values the first sweep leaves unchanged) or r, q, p copied by
             // the neighbours during the previous sweep
             if (lane == 0) {
+                // neighbours across a periodic y boundary: the last CTA's
+                // last row above row 0, the first CTA's first row below ny-1
                 const uint32_t rb = (uint32_t)px * 4u;
-                const bool top = c > 0, bot = c + 1 < G;
+                const bool top = c > 0 || wrap, bot = c + 1 < G || wrap;
+                const int ct = c > 0 ? c - 1 : G - 1, cb = c + 1 < G ? c + 1 : 0;
+                const int rt = row0 > 0 ? row0 - 1 : ny - 1, rbm = row1 < ny ? row1 : 0;
                 const uint32_t per = first ? rb : 3u * rb;
                 mbar_arrive_expect_tx(hfull, (top ? per : 0u) + (bot ? per : 0u));
                 if (first) {
-                    if (top) bulk_load(hrow(smem, 0, H_R), a.r + base + (long long)(row0 - 1) * px, rb, hfull);
-                    if (bot) bulk_load(hrow(smem, 1, H_R), a.r + base + (long long)row1 * px, rb, hfull);
+                    if (top) bulk_load(hrow(smem, 0, H_R), a.r + base + (long long)rt * px, rb, hfull);
+                    if (bot) bulk_load(hrow(smem, 1, H_R), a.r + base + (long long)rbm * px, rb, hfull);
                 } else {
                     for (int arr = 0; arr < 3; arr++) {
-                        if (top) bulk_load(hrow(smem, 0, arr), hb_row(a, ppar, c - 1, 1, arr, G, px), rb, hfull);
-                        if (bot) bulk_load(hrow(smem, 1, arr), hb_row(a, ppar, c + 1, 0, arr, G, px), rb, hfull);
+                        if (top) bulk_load(hrow(smem, 0, arr), hb_row(a, ppar, ct, 1, arr, G, px), rb, hfull);
+                        if (bot) bulk_load(hrow(smem, 1, arr), hb_row(a, ppar, cb, 0, arr, G, px), rb, hfull);
                     }
                 }
             }
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             }
             // p of row row0-1 from the top halo rows
             pn.zero();
-            if (c > 0 && act) {
+            if ((c > 0 || wrap) && act) {
                 F4 rv;
                 rv.ld(hrow(smem, 0, H_R) + cx);
                 if (first) {
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                 } else {
                     // me == row1: p of the first row of the CTA below
                     r_next.zero();
-                    if (c + 1 < G && act) {
+                    if ((c + 1 < G || wrap) && act) {
                         F4 rv;
                         rv.ld(hrow(smem, 1, H_R) + cx);
                         if (first) {
@@ -348,8 +355,9 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                         if (mt == row1 - 1) qv.st(hb_row(a, par, c, 1, H_Q, G, px) + cx);
                     }
                     mdown = gy;
-                } else if (act && row0 - 1 >= 0) {
-                    // t == -1: bond row row0-1 gives the down bonds of row0
+                } else if (act && (row0 - 1 >= 0 || wrap)) {
+                    // t == -1: bond row row0-1 (ny-1 across a periodic
+                    // boundary) gives the down bonds of row0
                     mdown.ld(stg(smem, b, A_GY) + cx);
                 }
                 __syncwarp();

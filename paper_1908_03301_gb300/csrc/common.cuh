@@ -8,10 +8,10 @@
 // neighbour offset), so the stencil never indexes outside an allocation.
 // Bond plane d over the padded grid holds at idx(c) the conductance of the
 // bond c -> c + e_d, and 0 where that bond does not exist.  Along a periodic
-// axis (y or z) the last layer's bonds lead back to layer 0; only the set-up
-// kernels, the FP64 residual pass and the compacted solve (whose neighbour
-// table holds the wrap) follow them, so periodic networks always take the
-// compacted solve.
+// axis (y or z) the last layer's bonds lead back to layer 0; the set-up
+// kernels, the FP64 residual pass, the persistent 2D kernel (periodic y) and
+// the compacted solve (whose neighbour table holds the wrap) follow them, and
+// periodic networks take only those two inner solves.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

@@ -201,20 +201,25 @@ bool use_sweep_kernel() {
 // The compacted solve replaces the lattice kernels when the unknowns are a
 // small part of the lattice (its list traffic is about twice a lattice
 // sweep's per node): below 35 % of the lattice nodes, or always with
-// NETSOLVE_KERNEL=compact.  Periodic networks always take it: its neighbour
-// table holds the wrap bonds, the lattice stencils do not.
-bool use_compact_kernel(const net_t *n, int) {
+// NETSOLVE_KERNEL=compact.  Of the lattice kernels only the persistent 2D
+// one follows a periodic (y) boundary; periodic networks it does not take
+// (3D, FP64 inner loop, wider than its rows) take the compacted solve, whose
+// neighbour table holds the wrap bonds.
+bool use_compact_kernel(const net_t *n, int f32) {
     if (n->n_solved <= 0) return false;
-    if (n->g.per) return true;
     const char *e = getenv("NETSOLVE_KERNEL");
-    if (e && strcmp(e, "compact") == 0) return true;
-    if (e && *e) return false;
+    const bool forced = e && strcmp(e, "compact") == 0;
     const long long lattice = (long long)n->g.nx * n->g.ny * n->g.nz;
-    return 100 * n->n_solved < 35 * lattice;
+    const bool sparse = 100 * n->n_solved < 35 * lattice;
+    if (n->g.per) return forced || sparse || !persist_applies(n->g, f32);
+    if (forced) return true;
+    if (e && *e) return false;
+    return sparse;
 }
 
 bool use_persist_kernel(const net_t *n, int f32) {
-    if (use_compact_kernel(n, f32) || n->g.per) return false;
+    if (use_compact_kernel(n, f32)) return false;
+    if (n->g.per) return persist_applies(n->g, f32);
     const char *e = getenv("NETSOLVE_KERNEL");
     if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0 || strcmp(e, "compact") == 0)) return false;
     return persist_applies(n->g, f32);

@@ -10,8 +10,10 @@
 //      non-negative float's bit pattern orders like its value (0 and -0 both
 //      map to key 0), so a histogram of the next digit over the keys that
 //      match the digits chosen so far finds the digit of the k-th smallest
-//      key; after 4 (FP32) or 8 (FP64) passes the k-th smallest key T and the
-//      number `need` of bonds equal to T that still have to close are known;
+//      key (one thread picks it on the device, so the passes run back to
+//      back); after 4 (FP32) or 8 (FP64) passes the k-th smallest key T and
+//      the number `need` of bonds equal to T that still have to close are
+//      known;
 //   2. every bond with key < T closes; of the bonds with key == T, the first
 //      `need` in position order close: all of them when need equals their
 //      count (the usual case for continuous values), otherwise a count per
@@ -55,16 +57,25 @@ __device__ __forceinline__ uint64_t key_of(double v) {
     return v == 0.0 ? 0ull : (uint64_t)__double_as_longlong(v);
 }
 
+// Selection state, in device memory between the passes: the digits of T
+// chosen so far, the rank still to find among the keys that match them, and
+// (after the last pass) how many keys equal T.
+struct RsState {
+    unsigned long long prefix, rem, count_T;
+    unsigned bad, pad_;
+};
+
 // Histogram of digit (key >> shift) & 255 over the keys whose bits above
-// shift + 8 equal `prefix` (all keys in the first pass).
+// shift + 8 equal the prefix chosen so far (all keys in the first pass).
 template <typename T, typename K>
-__global__ void __launch_bounds__(RT) rs_hist_kernel(Planes P, int shift, K prefix, int check,
+__global__ void __launch_bounds__(RT) rs_hist_kernel(Planes P, int shift, const RsState *state, int check,
                                                      unsigned long long *hist, unsigned *bad) {
     __shared__ unsigned h[256];
     for (int i = threadIdx.x; i < 256; i += RT) h[i] = 0u;
     __syncthreads();
     constexpr int BITS = 8 * sizeof(K);
     const bool all = shift + 8 >= BITS;
+    const K prefix = (K)state->prefix;
     const long long M = P.off[3];
     unsigned mybad = 0;
     for (long long t = blockIdx.x * (long long)RT + threadIdx.x; t < M; t += (long long)gridDim.x * RT) {
@@ -77,6 +88,18 @@ __global__ void __launch_bounds__(RT) rs_hist_kernel(Planes P, int shift, K pref
     for (int i = threadIdx.x; i < 256; i += RT)
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
     if (mybad) atomicOr(bad, 1u);
+}
+
+// One thread: the digit whose bin holds the rank still to find; the bins
+// are cleared for the next pass.
+__global__ void rs_select_kernel(unsigned long long *hist, RsState *state) {
+    unsigned long long rem = state->rem;
+    int b = 0;
+    while (b < 255 && hist[b] < rem) rem -= hist[b++];
+    state->prefix = (state->prefix << 8) | (unsigned long long)b;
+    state->rem = rem;
+    state->count_T = hist[b];
+    for (int i = 0; i < 256; i++) hist[i] = 0ull;
 }
 
 // Close every bond with key < T (and key == T when `with_equal`).
@@ -170,45 +193,45 @@ net_status close_smallest(const Planes &P, long long k, cudaStream_t cs) {
     const int nb = grid_for(M);
     net_status st_ = NET_OK;
     unsigned long long *hist = nullptr, *offs = nullptr;
-    unsigned *bad = nullptr, *counts = nullptr;
-    unsigned long long hh[256];
-    unsigned hbad = 0;
-    K prefix = 0;
-    unsigned long long rem = (unsigned long long)k, count_T = 0;
+    RsState *state = nullptr;
+    unsigned *counts = nullptr;
+    RsState hs{};
     std::vector<unsigned> hc;
     std::vector<unsigned long long> ho;
     long long nch = 0;
+    // all passes run back to back on the stream (the digit choice is made on
+    // the device); the host reads the state once, before anything is written
     RS_CK(cudaMallocAsync((void **)&hist, 256 * sizeof(unsigned long long), cs));
-    RS_CK(cudaMallocAsync((void **)&bad, sizeof(unsigned), cs));
-    RS_CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), cs));
+    RS_CK(cudaMallocAsync((void **)&state, sizeof(RsState), cs));
+    RS_CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), cs));
+    hs.rem = (unsigned long long)k;
+    RS_CK(cudaMemcpyAsync(state, &hs, sizeof(RsState), cudaMemcpyHostToDevice, cs));
     for (int shift = BITS - 8; shift >= 0; shift -= 8) {
         const int first = shift == BITS - 8;
-        RS_CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), cs));
-        rs_hist_kernel<T, K><<<nb, RT, 0, cs>>>(P, shift, prefix, first, hist, bad);
+        rs_hist_kernel<T, K><<<nb, RT, 0, cs>>>(P, shift, state, first, hist, &state->bad);
         RS_CK(cudaGetLastError());
-        RS_CK(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, cs));
-        if (first) RS_CK(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, cs));
-        RS_CK(cudaStreamSynchronize(cs));
-        if (hbad) {
-            set_error("net_close_smallest: a conductance is negative, NaN or infinite");
-            st_ = NET_EINVAL;
-            goto done;
-        }
-        if (k == 0) goto done;  // conductances checked, nothing to close
-        int b = 0;
-        while (b < 255 && hh[b] < rem) rem -= hh[b++];
-        prefix = (K)((prefix << 8) | (K)b);
-        count_T = hh[b];
+        if (k == 0) break;  // only the conductance check
+        rs_select_kernel<<<1, 1, 0, cs>>>(hist, state);
+        RS_CK(cudaGetLastError());
     }
-    // prefix = T, the k-th smallest key; rem of the count_T bonds equal to T close
-    if (rem == count_T) {
-        rs_close_kernel<T, K><<<nb, RT, 0, cs>>>(P, prefix, 1);
+    RS_CK(cudaMemcpyAsync(&hs, state, sizeof(RsState), cudaMemcpyDeviceToHost, cs));
+    RS_CK(cudaStreamSynchronize(cs));
+    if (hs.bad) {
+        set_error("net_close_smallest: a conductance is negative, NaN or infinite");
+        st_ = NET_EINVAL;
+        goto done;
+    }
+    if (k == 0) goto done;
+    // T = hs.prefix, the k-th smallest key; hs.rem of the hs.count_T bonds
+    // equal to T close
+    if (hs.rem == hs.count_T) {
+        rs_close_kernel<T, K><<<nb, RT, 0, cs>>>(P, (K)hs.prefix, 1);
         RS_CK(cudaGetLastError());
     } else {
         nch = (M + CHUNK - 1) / CHUNK;
         RS_CK(cudaMallocAsync((void **)&counts, sizeof(unsigned) * (size_t)nch, cs));
         RS_CK(cudaMallocAsync((void **)&offs, sizeof(unsigned long long) * (size_t)nch, cs));
-        rs_tie_count_kernel<T, K><<<(unsigned)nch, RT, 0, cs>>>(P, prefix, counts);
+        rs_tie_count_kernel<T, K><<<(unsigned)nch, RT, 0, cs>>>(P, (K)hs.prefix, counts);
         RS_CK(cudaGetLastError());
         hc.resize((size_t)nch);
         ho.resize((size_t)nch);
@@ -220,13 +243,13 @@ net_status close_smallest(const Planes &P, long long k, cudaStream_t cs) {
             run += hc[(size_t)c];
         }
         RS_CK(cudaMemcpyAsync(offs, ho.data(), sizeof(unsigned long long) * (size_t)nch, cudaMemcpyHostToDevice, cs));
-        rs_tie_close_kernel<T, K><<<(unsigned)nch, RT, 0, cs>>>(P, prefix, offs, rem);
+        rs_tie_close_kernel<T, K><<<(unsigned)nch, RT, 0, cs>>>(P, (K)hs.prefix, offs, hs.rem);
         RS_CK(cudaGetLastError());
     }
     RS_CK(cudaStreamSynchronize(cs));
 done:
     if (hist) cudaFreeAsync(hist, cs);
-    if (bad) cudaFreeAsync(bad, cs);
+    if (state) cudaFreeAsync(state, cs);
     if (counts) cudaFreeAsync(counts, cs);
     if (offs) cudaFreeAsync(offs, cs);
     cudaStreamSynchronize(cs);

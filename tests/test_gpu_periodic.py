@@ -40,8 +40,14 @@ CASES = [((64, 50), 0, (1,), 0.58, 1), ((41, 37), 0, (1,), 1.0, 2),
 
 
 @pytest.mark.parametrize("dims,f,per,p,seed", CASES)
-@pytest.mark.parametrize("precision,refine", [(0, 0), (1, 0), (0, 1)])
-def test_periodic_matches_oracle(ns, dims, f, per, p, seed, precision, refine):
+@pytest.mark.parametrize("precision,refine,kernel", [(0, 0, ""), (1, 0, ""), (0, 1, ""),
+                                                     (0, 0, "compact"), (0, 1, "compact")])
+def test_periodic_matches_oracle(ns, monkeypatch, dims, f, per, p, seed, precision, refine, kernel):
+    """Dense 2D periodic networks take the persistent kernel (wrap rows in its
+    halo exchange) unless the compacted solve is forced; 3D ones, FP64 and
+    sparse ones take the compacted solve."""
+    if kernel:
+        monkeypatch.setenv("NETSOLVE_KERNEL", kernel)
     planes = periodic_net(dims, per, p, seed)
     ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13, periodic=per)
     lab_o, cls_o = oracle.labels(dims, planes, flow_axis=f, periodic=per)
