@@ -1,4 +1,6 @@
-"""ctypes front end of the plain-C FP64 oracle (``netoracle.c``).
+"""ctypes front end of the plain-C FP64 oracle (``netoracle.c``), plus the
+numpy oracles of the input-side steps: sorted-removal percolation and the FBM
+generator (Eq. 1, Eq. 2) with its conductance map.
 
 Test infrastructure: the CUDA solver never imports this module.
 
@@ -195,4 +197,53 @@ def close_smallest(planes, q):
         c = closed[o:o + g.size].reshape(g.shape)
         out.append(np.where(c, g.dtype.type(0), g))
         o += g.size
+    return out
+
+
+def fbm_field(noise, hurst, beta=None):
+    """Fractional Brownian motion by spectral filtering (Eq. 1, Eq. 2).
+
+    ``noise``: complex white noise, node-shaped (numpy order (z, y, x)); the
+    random draws are an input.  Each Fourier mode is weighted by the square
+    root of the spectral density, S ~ (sum_a beta_a w_a^2)^-(H + d/2) with
+    w_a the discrete frequencies (cycles per node, numpy's fftfreq) and d the
+    dimension (Eq. 1: d = 2 and beta = 1 give (w_x^2 + w_y^2)^-(H+1); Eq. 2:
+    the anisotropic betas); the zero mode is dropped.  The field is the real
+    part of the inverse transform, shifted and scaled to zero mean and unit
+    variance (population).  ``beta`` is per lattice axis (x, y[, z]), default 1.
+    """
+    noise = np.asarray(noise, dtype=np.complex128)
+    shape = noise.shape
+    d = len(shape)
+    if beta is None:
+        beta = (1.0,) * d
+    k2 = np.zeros(shape)
+    for ax in range(d):
+        lattice_axis = d - 1 - ax           # numpy axis ax is lattice axis d-1-ax
+        w = np.fft.fftfreq(shape[ax])
+        sh = [1] * d
+        sh[ax] = shape[ax]
+        k2 = k2 + float(beta[lattice_axis]) * (w * w).reshape(sh)
+    k2.flat[0] = 1.0
+    amp = k2 ** (-(2.0 * hurst + d) / 4.0)
+    amp.flat[0] = 0.0
+    field = np.fft.ifftn(noise * amp).real
+    field = field - field.mean()
+    sd = np.sqrt(np.mean(field * field))
+    return field / sd if sd > 0 else field
+
+
+def fbm_bonds(field, sigma):
+    """Conductances g = exp(sigma * B_b), B_b the mean of the bond's two end
+    nodes of the field (the workloads' map); planes in the project's layout."""
+    field = np.asarray(field, dtype=np.float64)
+    nd = field.ndim
+    out = []
+    for d in range(nd):
+        ax = nd - 1 - d
+        lo = [slice(None)] * nd
+        hi = [slice(None)] * nd
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        out.append(np.exp(sigma * 0.5 * (field[tuple(lo)] + field[tuple(hi)])))
     return out

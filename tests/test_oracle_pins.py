@@ -512,3 +512,85 @@ def test_close_smallest_invariants():
         assert all(o.dtype == np.float32 for o in out)
     with pytest.raises(ValueError):
         oracle.close_smallest(planes, 1.5)
+
+
+# ---------------------------------------------------------------- FBM generator (Eq. 1, Eq. 2)
+def _modes(shape, modes):
+    noise = np.zeros(shape, complex)
+    for idx in modes:
+        noise[idx] = 1.0
+    return noise
+
+
+def test_fbm_single_mode_is_a_cosine():
+    """One Fourier mode: the normalised field is sqrt(2) cos(2 pi k.x / n)
+    (frequency convention, real part and normalisation; the weight cancels)."""
+    ny, nx = 16, 24
+    f = oracle.fbm_field(_modes((ny, nx), [(5, 20)]), 0.7)
+    y, x = np.mgrid[0:ny, 0:nx]
+    want = np.sqrt(2.0) * np.cos(2 * np.pi * (5 * y / ny + 20 * x / nx))
+    np.testing.assert_allclose(f, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape,H,beta,modes", [
+    ((16, 24), 0.7, (2.0, 0.5), [(0, 3), (2, 0), (5, 20)]),
+    ((12, 10, 14), 0.3, (1.0, 3.0, 0.25), [(0, 0, 2), (0, 3, 0), (4, 0, 0), (11, 7, 12)])])
+def test_fbm_mode_weights_follow_the_spectral_density(shape, H, beta, modes):
+    """Several modes with unit noise: each mode's cosine coefficient is
+    proportional to S(w)^(1/2) = (sum_a beta_a w_a^2)^-(H/2 + d/4): the ratio
+    of coefficients pins the exponent, the betas and the axis order."""
+    d = len(shape)
+    f = oracle.fbm_field(_modes(shape, modes), H, beta)
+    grids = np.meshgrid(*[np.arange(m) for m in shape], indexing="ij")
+    coef, amp = [], []
+    for idx in modes:
+        phase = sum(2 * np.pi * idx[ax] * grids[ax] / shape[ax] for ax in range(d))
+        coef.append(2.0 * np.mean(f * np.cos(phase)))
+        k2 = 0.0
+        for ax in range(d):
+            w = idx[ax] / shape[ax]
+            w = w - 1.0 if w > 0.5 else w
+            k2 += beta[d - 1 - ax] * w * w
+        amp.append(k2 ** (-(2 * H + d) / 4))
+    for i in range(1, len(modes)):
+        assert abs(coef[i] / coef[0] - amp[i] / amp[0]) <= 1e-10 * amp[i] / amp[0]
+
+
+def test_fbm_spectrum_slope_eq1():
+    """Isotropic 2D field from white noise: the radially averaged power
+    spectrum falls as |w|^-(2H+2) (Eq. 1)."""
+    gen = netgen.rng(9500)
+    n, H = 512, 0.7
+    noise = gen.standard_normal((n, n)) + 1j * gen.standard_normal((n, n))
+    f = oracle.fbm_field(noise, H)
+    P = np.abs(np.fft.fft2(f)) ** 2
+    w = np.sqrt(np.add.outer(np.fft.fftfreq(n) ** 2, np.fft.fftfreq(n) ** 2))
+    bins = np.geomspace(4.0 / n, 0.4, 12)
+    lw, lp = [], []
+    for a, b in zip(bins[:-1], bins[1:]):
+        m = (w >= a) & (w < b)
+        lw.append(np.log(w[m].mean()))
+        lp.append(np.log(P[m].mean()))
+    slope = np.polyfit(lw, lp, 1)[0]
+    assert abs(slope + (2 * H + 2)) < 0.1
+
+
+def test_fbm_anisotropy_layers_parallel_to_x():
+    """beta_x / beta_y > 1 damps modes that vary along x: the field is
+    smoother along x than along y (layers parallel to x, Eq. 2)."""
+    gen = netgen.rng(9501)
+    noise = gen.standard_normal((256, 256)) + 1j * gen.standard_normal((256, 256))
+    f = oracle.fbm_field(noise, 0.5, beta=(5.0, 1.0))
+    dx = np.mean(np.diff(f, axis=1) ** 2)
+    dy = np.mean(np.diff(f, axis=0) ** 2)
+    assert dx < 0.5 * dy
+    g = oracle.fbm_field(noise, 0.5, beta=(1.0, 1.0))
+    np.testing.assert_allclose(g, oracle.fbm_field(noise, 0.5), rtol=0, atol=1e-13)
+    assert abs(f.mean()) < 1e-12 and abs(np.mean(f * f) - 1.0) < 1e-12
+
+
+def test_fbm_bonds_hand_values():
+    B = np.array([[0.0, 1.0, -1.0], [2.0, 0.5, 0.0]])  # (ny, nx) = (2, 3)
+    gx, gy = oracle.fbm_bonds(B, 2.0)
+    np.testing.assert_allclose(gx, np.exp(2.0 * np.array([[0.5, 0.0], [1.25, 0.25]])), rtol=1e-15)
+    np.testing.assert_allclose(gy, np.exp(2.0 * np.array([[1.0, 0.75, -0.5]])), rtol=1e-15)
