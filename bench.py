@@ -44,10 +44,13 @@ def args_():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fbm2048",
-                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic", "corrperc"],
+                    choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic", "corrperc",
+                             "fbmgen"],
                     help="fbm2048: the headline 2048^2 solve; perc3d: 256^3 percolation; batch: "
                          "512 networks in one batched solve; serve: the request queue; aniso: "
                          "K_x/K_y of anisotropic FBM networks (both axes batched)")
+    ap.add_argument("--fbm-log2", default="24,28,30",
+                    help="fbmgen: log2 of the node counts (even), comma separated")
     ap.add_argument("--aniso-size", type=int, default=512)
     ap.add_argument("--aniso-real", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=512)
@@ -745,6 +748,67 @@ def run_corrperc(a):
     print(json.dumps(line), flush=True)
 
 
+def run_fbmgen(a):
+    """The FBM generator (Eq. 1) at the array sizes of the paper's Table I
+    (2^24, 2^28 and 2^30 nodes: 4096^2, 16384^2, 32768^2), H = 0.7: noise ->
+    filter -> inverse FFT -> normalised field -> FP32 conductance planes
+    (sigma = 1.5), all on the device, with the FP32 transform (the value) and
+    the FP64 one beside it.  The complex noise is drawn on the device before
+    the timed region (the random draws are the generator's input).  Table I's
+    times (MPI on four processes, with their random draws) are context only."""
+    import torch
+
+    from paper_1908_03301_gb300 import netsolve as ns
+
+    ns.lib(build_if_missing=True)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    paper_mpi_s = {24: 0.4, 28: 2.7, 30: 20.6}
+    rows = []
+    for lg in [int(v) for v in a.fbm_log2.split(",")]:
+        n = 1 << (lg // 2)
+        dims = (n, n)
+        gen = torch.Generator(device=dev).manual_seed(netgen_seed(7) + lg)
+        field = torch.empty((n, n), dtype=torch.float64, device=dev)
+        row = {"nodes": n * n, "log2_nodes": lg, "paper_table1_mpi_s": paper_mpi_s.get(lg)}
+        for tag, cdt in (("fft_f32", torch.complex64), ("fft_f64", torch.complex128)):
+            ms_f, ms_b = [], []
+            for it in range(a.warmup + a.steps):
+                noise = torch.randn((n, n), dtype=cdt, device=dev, generator=gen)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                ns.fbm_field(dims, noise, 0.7, out=field)
+                e[1].record(stream)
+                planes = ns.fbm_bonds(dims, field, 1.5, torch.float32)
+                e[2].record(stream)
+                torch.cuda.synchronize()
+                if it >= a.warmup:
+                    ms_f.append(e[0].elapsed_time(e[1]))
+                    ms_b.append(e[1].elapsed_time(e[2]))
+                del noise, planes
+            row[tag] = {"field_ms": statistics.mean(ms_f), "bonds_ms": statistics.mean(ms_b),
+                        "total_ms": statistics.mean(ms_f) + statistics.mean(ms_b),
+                        "field_check": {"mean": float(field.mean()), "var": float((field * field).mean())}}
+        rows.append(row)
+        del field
+        torch.cuda.empty_cache()
+    total = sum(r["fft_f32"]["total_ms"] for r in rows)
+    line = {"metric": METRIC, "workload": "fbmgen", "value": len(rows) / (total / 1e3),
+            "unit": "fields/s", "steps": a.steps, "warmup": a.warmup, "dtype": "f32 (FFT), f32 planes",
+            "data": "synthetic",
+            "config": {"workload": "2D FBM fields of 2^24, 2^28, 2^30 nodes, H=0.7, Eq. 1 spectral "
+                                   "filtering + inverse FFT (cuFFT C2C FP32; Z2Z FP64 beside it) + "
+                                   "normalisation, then FP32 conductance planes exp(1.5 (B_i+B_j)/2)"},
+            "sizes": rows}
+    print(json.dumps(line), flush=True)
+
+
+def netgen_seed(k):
+    from paper_1908_03301_gb300 import netgen
+
+    return netgen.SEED_BASE + k
+
+
 def main():
     a = args_()
     if a.profile_solve:
@@ -753,10 +817,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if a.workload in ("perc3d", "serve", "aniso", "periodic", "corrperc") and a.impl == "ours":
+    if a.workload in ("perc3d", "serve", "aniso", "periodic", "corrperc", "fbmgen") and a.impl == "ours":
         if rank == 0:
             {"perc3d": run_perc3d, "serve": run_serve, "aniso": run_aniso,
-             "periodic": run_periodic, "corrperc": run_corrperc}[a.workload](a)
+             "periodic": run_periodic, "corrperc": run_corrperc, "fbmgen": run_fbmgen}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)

@@ -290,6 +290,49 @@ net_status net_labels_noalloc(const net_desc *desc, const void *const g[3], int3
 net_status net_close_smallest(const net_desc *desc, void *const g[3], double q);
 
 /*
+ * Fractional Brownian motion field by spectral filtering (Eq. 1, Eq. 2), the
+ * generator of the paper's correlated networks.  The random draws are an
+ * input: complex white noise, one value per node.  Each Fourier mode is
+ * weighted by sqrt(S(w)), S(w) = (sum_a beta_a w_a^2)^-(H + d/2) (d = ndim;
+ * Eq. 1 is d = 2 with beta = 1, Eq. 2 the anisotropic case), with w_a the
+ * discrete frequency in cycles per node (0, 1, .., ceil(n/2)-1, -floor(n/2),
+ * .., -1 over n) and the zero mode dropped; the field is the real part of the
+ * inverse FFT, shifted and scaled to zero mean and unit variance.
+ *   d       extents, H, per-axis beta (> 0, finite) and the stream (NULL =
+ *           the default stream); read during the call only.
+ *   noise   device array of N complex values (real, imaginary interleaved;
+ *           double, or float with fft_f32), node order x fastest; overwritten
+ *           (it holds the transform).
+ *   field   device array of N doubles, the field (output).
+ * N = nx*ny*nz < 2^31.  The FFT is cuFFT's (loaded on first use; NET_ECUDA
+ * if it cannot be loaded), with its plan and workspace allocated and freed
+ * in the call.  Returns after the work has finished.  NET_EINVAL for bad
+ * extents, a non-finite H or a bad beta.
+ */
+typedef struct {
+    int ndim;          /* 2 or 3 */
+    int64_t n[3];      /* node extents (nx, ny, nz); n[2] = 1 in 2D */
+    double hurst;      /* Hurst exponent H */
+    double beta[3];    /* anisotropy per axis (x, y, z); all 1 for Eq. 1 */
+    int fft_f32;       /* 0: noise is complex double and the transform FP64;
+                          1: complex float noise and an FP32 transform (GB300
+                          runs FP64 arithmetic at 1/64 of the FP32 rate) */
+    void *stream;      /* cudaStream_t; NULL = the default stream */
+} net_fbm_desc;
+net_status net_fbm_field(const net_fbm_desc *d, void *noise, double *field);
+
+/*
+ * Conductances from a field B (device, N doubles, node order x fastest):
+ * g = exp(sigma * (B_i + B_j) / 2) for the bond between nodes i and j,
+ * written into the bond planes g[d] (device, desc->bond_dtype, the layout of
+ * net_create including periodic planes).  desc as for net_create with
+ * on_device = 1; the work runs on desc->stream and has finished when the
+ * call returns.  NET_EINVAL for a bad descriptor, a NULL plane or a
+ * non-finite sigma.
+ */
+net_status net_fbm_bonds(const net_desc *desc, const double *field, double sigma, void *const g[3]);
+
+/*
  * Solve `count` independent networks together.  Every sweep of the CG loop
  * (Sec. IV) is one launch of a kernel with one CTA per SM that walks all
  * running networks' segments; each network keeps its own CG scalars and its

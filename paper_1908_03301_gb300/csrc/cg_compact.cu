@@ -34,7 +34,8 @@ namespace {
 
 constexpr int CT = 512;                 // threads per CTA
 constexpr int CW = CT / 32;
-constexpr int UNR = 2;                  // unknowns a thread keeps in flight
+constexpr int UNR = 2;                  // unknowns a thread keeps in flight (FP64)
+constexpr int UNR32 = 2;                // the same in FP32
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
@@ -229,7 +230,6 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
     __shared__ T s_red[CW][4];
     const int G = gridDim.x, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long U = a.n;
     T *__restrict__ y = (T *)a.y;
     T *__restrict__ r = (T *)a.r;
     T *p = (T *)a.p;
@@ -243,18 +243,21 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
         for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = src[k];
     }
     __syncthreads();
-    const long long tid = (long long)c * CT + threadIdx.x, nth = (long long)G * CT;
+    // list indices fit in 32 bits (the table stores them as int)
+    const int tid = c * CT + (int)threadIdx.x, nth = G * CT;
+    const int U = (int)a.n;
+    constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
     unsigned target = 0;
     bool bad = false;
     while (st.stop == 0) {
         const bool first = st.iter == 0;
         const T alpha = (T)st.alpha, beta = (T)st.beta;
-        // ---- phase A: finish iteration k-1 (UNR unknowns in flight per thread) ----
-        for (long long k0 = tid; k0 < U; k0 += UNR * nth) {
-            T rk[UNR], pk[UNR], qk[UNR], yk[UNR];
+        // ---- phase A: finish iteration k-1 (UN unknowns in flight per thread) ----
+        for (int k0 = tid; k0 < U; k0 += UN * nth) {
+            T rk[UN], pk[UN], qk[UN], yk[UN];
 #pragma unroll
-            for (int u = 0; u < UNR; u++) {
-                const long long k = k0 + u * nth;
+            for (int u = 0; u < UN; u++) {
+                const int k = k0 + u * nth;
                 if (k < U) {
                     rk[u] = r[k];
                     if (!first) {
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < UNR; u++) {
-                const long long k = k0 + u * nth;
+            for (int u = 0; u < UN; u++) {
+                const int k = k0 + u * nth;
                 if (k >= U) continue;
                 if (first) {
                     p[k] = rk[u];
@@ -289,14 +292,14 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
         // ---- phase B: q = A p and the four sums ----
         T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
         const long long VS = U + 1;  // val slot stride
-        for (long long k0 = tid; k0 < U; k0 += UNR * nth) {
-            T wxp[UNR], wxm[UNR], wp[UNR][NDIM - 1];
-            int ip[UNR][NDIM - 1], im[UNR][NDIM - 1];
+        for (int k0 = tid; k0 < U; k0 += UN * nth) {
+            T wxp[UN], wxm[UN], wp[UN][NDIM - 1];
+            int ip[UN][NDIM - 1], im[UN][NDIM - 1];
 #pragma unroll
-            for (int u = 0; u < UNR; u++) {
-                const long long k = k0 + u * nth;
+            for (int u = 0; u < UN; u++) {
+                const int k = k0 + u * nth;
                 const bool ok = k < U;
-                const long long kk = ok ? k : 0;
+                const int kk = ok ? k : 0;
                 wxp[u] = ok ? __ldg(val + kk) : T(0);
                 wxm[u] = (ok && k > 0) ? __ldg(val + kk - 1) : T(0);
 #pragma unroll
@@ -307,8 +310,8 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < UNR; u++) {
-                const long long k = k0 + u * nth;
+            for (int u = 0; u < UN; u++) {
+                const int k = k0 + u * nth;
                 if (k >= U) continue;
                 const T pk = __ldcg(p + k);
                 T nb = wxp[u] * __ldcg(p + k + 1);

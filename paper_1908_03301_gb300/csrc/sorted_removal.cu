@@ -77,12 +77,23 @@ __global__ void __launch_bounds__(RT) rs_hist_kernel(Planes P, int shift, const 
     const bool all = shift + 8 >= BITS;
     const K prefix = (K)state->prefix;
     const long long M = P.off[3];
+    const int lane = threadIdx.x & 31;
     unsigned mybad = 0;
-    for (long long t = blockIdx.x * (long long)RT + threadIdx.x; t < M; t += (long long)gridDim.x * RT) {
-        const T v = *elem<T>(P, t);
-        if (check && (!(v >= T(0)) || isinf(v))) mybad = 1u;
-        const K k = key_of(v);
-        if (all || (k >> (shift + 8)) == prefix) atomicAdd(&h[(unsigned)(k >> shift) & 255u], 1u);
+    // The leading digits of a conductance field fall in a few bins, so the
+    // lanes of a warp that share a bin add once (a warp-wide match); the
+    // loop runs warp-uniformly so every lane takes part in the match.
+    for (long long base = blockIdx.x * (long long)RT + (threadIdx.x & ~31); base < M;
+         base += (long long)gridDim.x * RT) {
+        const long long t = base + lane;
+        int bin = -1;
+        if (t < M) {
+            const T v = *elem<T>(P, t);
+            if (check && (!(v >= T(0)) || isinf(v))) mybad = 1u;
+            const K k = key_of(v);
+            if (all || (k >> (shift + 8)) == prefix) bin = (int)((unsigned)(k >> shift) & 255u);
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(same) - 1) atomicAdd(&h[bin], (unsigned)__popc(same));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += RT)

@@ -59,11 +59,16 @@ class net_tune(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class net_fbm_desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 3), ("hurst", C.c_double),
+                ("beta", C.c_double * 3), ("fft_f32", C.c_int), ("stream", C.c_void_p)]
+
+
 EXPORTS = ["net_opts_default", "net_create", "net_solve", "net_flux", "net_get_pressure",
            "net_get_labels", "net_destroy", "net_solve_batch", "netq_create", "netq_submit",
            "netq_poll", "netq_wait", "netq_cancel", "netq_stats", "netq_destroy",
            "net_last_error", "net_labels_noalloc", "net_autotune", "net_tune_clear",
-           "net_get_backbone", "net_close_smallest"]
+           "net_get_backbone", "net_close_smallest", "net_fbm_field", "net_fbm_bonds"]
 
 _lib = None
 
@@ -103,6 +108,10 @@ def lib(build_if_missing: bool = False):
     L.net_labels_noalloc.restype = C.c_int
     L.net_close_smallest.argtypes = [P(net_desc), P(vp), C.c_double]
     L.net_close_smallest.restype = C.c_int
+    L.net_fbm_field.argtypes = [P(net_fbm_desc), vp, vp]
+    L.net_fbm_field.restype = C.c_int
+    L.net_fbm_bonds.argtypes = [P(net_desc), vp, C.c_double, P(vp)]
+    L.net_fbm_bonds.restype = C.c_int
     L.net_autotune.argtypes = [P(vp), C.c_int, P(net_opts), P(net_tune)]
     L.net_autotune.restype = C.c_int
     L.net_tune_clear.argtypes = []
@@ -352,6 +361,53 @@ def close_smallest(dims, planes, q, periodic=(), flow_axis=0):
     keep, ptrs, bdt, dev, stream = marshal_planes(planes, len(dims))
     desc = make_desc(dims, flow_axis, 1.0, 0.0, bdt, 1, stream, periodic)
     _check(lib().net_close_smallest(C.byref(desc), ptrs, float(q)), "net_close_smallest")
+    return planes
+
+
+def fbm_field(dims, noise, hurst, beta=None, out=None):
+    """net_fbm_field: FBM field (Eq. 1 / Eq. 2) from complex noise, a torch
+    complex128 (FP64 transform) or complex64 (FP32 transform) CUDA tensor of
+    node shape (it is overwritten).  Returns a float64 CUDA tensor of node
+    shape (``out`` if given)."""
+    import torch
+
+    if not (_is_torch(noise) and noise.is_cuda and noise.dtype in (torch.complex128, torch.complex64)
+            and noise.is_contiguous()):
+        raise TypeError("noise must be a contiguous complex128 or complex64 CUDA tensor")
+    f32 = int(noise.dtype == torch.complex64)
+    N = int(np.prod(dims))
+    if noise.numel() != N:
+        raise ValueError(f"noise has {noise.numel()} values, expected {N}")
+    if out is None:
+        out = torch.empty(tuple(reversed([int(v) for v in dims])), dtype=torch.float64, device=noise.device)
+    if not (out.dtype == torch.float64 and out.is_cuda and out.is_contiguous() and out.numel() == N):
+        raise ValueError("out must be a contiguous float64 CUDA tensor with one value per node")
+    n = list(int(v) for v in dims) + [1] * (3 - len(dims))
+    b = list(beta) if beta is not None else [1.0] * len(dims)
+    b = [float(v) for v in b] + [1.0] * (3 - len(b))
+    stream = torch.cuda.current_stream(noise.device).cuda_stream
+    d = net_fbm_desc(len(dims), (C.c_int64 * 3)(*n), float(hurst), (C.c_double * 3)(*b), f32, stream)
+    _check(lib().net_fbm_field(C.byref(d), noise.data_ptr(), out.data_ptr()), "net_fbm_field")
+    return out
+
+
+def fbm_bonds(dims, field, sigma, dtype=None, periodic=(), flow_axis=0):
+    """net_fbm_bonds: conductance planes exp(sigma (B_i + B_j)/2) from a
+    float64 CUDA field; returns torch CUDA planes of ``dtype`` (float64)."""
+    import torch
+
+    dtype = dtype or torch.float64
+    if not (_is_torch(field) and field.is_cuda and field.dtype == torch.float64 and field.is_contiguous()):
+        raise TypeError("field must be a contiguous float64 CUDA tensor")
+    planes = []
+    for d in range(len(dims)):
+        n = [int(v) for v in dims]
+        if d not in periodic:
+            n[d] -= 1
+        planes.append(torch.empty(tuple(reversed(n)), dtype=dtype, device=field.device))
+    keep, ptrs, bdt, dev, stream = marshal_planes(planes, len(dims))
+    desc = make_desc(dims, flow_axis, 1.0, 0.0, bdt, 1, stream, periodic)
+    _check(lib().net_fbm_bonds(C.byref(desc), field.data_ptr(), float(sigma), ptrs), "net_fbm_bonds")
     return planes
 
 

@@ -68,6 +68,14 @@ def test_host_side_validation_without_gpu(so):
     assert L.net_destroy(None) == ns.NET_OK
     assert L.net_autotune(None, 0, None, None) == ns.NET_EINVAL
     L.net_tune_clear()
+    # FBM generator: descriptor checks before any device work
+    one = ctypes.c_void_p(16)
+    for nd, n, H, beta in [(1, (8, 1, 1), 0.7, (1, 1, 1)), (2, (8, 8, 2), 0.7, (1, 1, 1)),
+                           (2, (8, 8, 1), float("nan"), (1, 1, 1)), (2, (8, 8, 1), 0.7, (0, 1, 1)),
+                           (3, (8, 8, 0), 0.7, (1, 1, 1))]:
+        fd = ns.net_fbm_desc(nd, (ctypes.c_int64 * 3)(*n), H, (ctypes.c_double * 3)(*beta), 0, None)
+        assert L.net_fbm_field(ctypes.byref(fd), one, one) == ns.NET_EINVAL
+        assert L.net_last_error()
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -76,7 +84,7 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_1908_03301_gb300 import netsolve as ns
 
     structs = {"net_desc": ns.net_desc, "net_opts": ns.net_opts, "net_result": ns.net_result,
-               "net_tune": ns.net_tune}
+               "net_tune": ns.net_tune, "net_fbm_desc": ns.net_fbm_desc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "netsolve.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
