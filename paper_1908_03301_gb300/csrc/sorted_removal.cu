@@ -10,7 +10,7 @@
 //      non-negative float's bit pattern orders like its value (0 and -0 both
 //      map to key 0), so a histogram of the next digit over the keys that
 //      match the digits chosen so far finds the digit of the k-th smallest
-//      key (one thread picks it on the device, so the passes run back to
+//      key (one warp picks it on the device, so the passes run back to
 //      back); after 4 (FP32) or 8 (FP64) passes the k-th smallest key T and
 //      the number `need` of bonds equal to T that still have to close are
 //      known;
@@ -101,16 +101,38 @@ __global__ void __launch_bounds__(RT) rs_hist_kernel(Planes P, int shift, const 
     if (mybad) atomicOr(bad, 1u);
 }
 
-// One thread: the digit whose bin holds the rank still to find; the bins
-// are cleared for the next pass.
+// One warp: the digit whose bin holds the rank still to find (lane l scans
+// bins 8l .. 8l+7 after a warp prefix sum of the lanes' totals); the bins are
+// cleared for the next pass.
 __global__ void rs_select_kernel(unsigned long long *hist, RsState *state) {
-    unsigned long long rem = state->rem;
-    int b = 0;
-    while (b < 255 && hist[b] < rem) rem -= hist[b++];
-    state->prefix = (state->prefix << 8) | (unsigned long long)b;
-    state->rem = rem;
-    state->count_T = hist[b];
-    for (int i = 0; i < 256; i++) hist[i] = 0ull;
+    const int lane = threadIdx.x;
+    unsigned long long c[8], own = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        c[j] = hist[lane * 8 + j];
+        own += c[j];
+    }
+    unsigned long long incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long want = state->rem;
+    const unsigned long long excl = incl - own;
+    // the lane holding the rank; the last lane if the counts fall short (the
+    // bins then end the search at 255, as a sequential scan would)
+    if ((excl < want && want <= incl) || (lane == 31 && want > total)) {
+        unsigned long long rem = want - excl;
+        int j = 0;
+        while (j < 7 && c[j] < rem) rem -= c[j++];
+        state->prefix = (state->prefix << 8) | (unsigned long long)(lane * 8 + j);
+        state->rem = rem;
+        state->count_T = c[j];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8; j++) hist[lane * 8 + j] = 0ull;
 }
 
 // Close every bond with key < T (and key == T when `with_equal`).
@@ -222,7 +244,7 @@ net_status close_smallest(const Planes &P, long long k, cudaStream_t cs) {
         rs_hist_kernel<T, K><<<nb, RT, 0, cs>>>(P, shift, state, first, hist, &state->bad);
         RS_CK(cudaGetLastError());
         if (k == 0) break;  // only the conductance check
-        rs_select_kernel<<<1, 1, 0, cs>>>(hist, state);
+        rs_select_kernel<<<1, 32, 0, cs>>>(hist, state);
         RS_CK(cudaGetLastError());
     }
     RS_CK(cudaMemcpyAsync(&hs, state, sizeof(RsState), cudaMemcpyDeviceToHost, cs));
