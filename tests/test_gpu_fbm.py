@@ -82,6 +82,21 @@ def test_fbm_bonds_match_oracle(ns, per, dtype):
         np.testing.assert_allclose(got, w.astype(got.dtype), rtol=rt)
 
 
+def test_fbm_bonds_3d_periodic(ns):
+    """3D planes with periodic y and z: the wrap layers join the last and
+    first node layers of the field."""
+    import torch
+
+    dims, per = (20, 17, 13), (1, 2)
+    field = oracle.fbm_field(_noise((13, 17, 20), 9), 0.4)
+    planes = ns.fbm_bonds(dims, torch.from_numpy(field).cuda(), 0.8, periodic=per)
+    want = [np.exp(0.4 * (field[:, :, :-1] + field[:, :, 1:])),
+            np.exp(0.4 * (field + np.roll(field, -1, axis=1))),
+            np.exp(0.4 * (field + np.roll(field, -1, axis=0)))]
+    for g, w in zip(planes, want):
+        np.testing.assert_allclose(g.cpu().numpy(), w, rtol=1e-14)
+
+
 def test_fbm_network_chain_matches_oracle(ns):
     """noise -> field -> conductances -> solve on the device, against the
     oracle's field, map and solve (Sec. II's correlated network)."""
