@@ -754,8 +754,9 @@ def run_fbmgen(a):
     filter -> inverse FFT -> normalised field -> FP32 conductance planes
     (sigma = 1.5), all on the device, with the FP32 transform (the value) and
     the FP64 one beside it.  The complex noise is drawn on the device before
-    the timed region (the random draws are the generator's input).  Table I's
-    times (MPI on four processes, with their random draws) are context only."""
+    the timed region (the random draws are the generator's input); the draw's
+    own time (torch's generator) is reported beside it, since Table I's times
+    (MPI on four processes, context only) include their random draws."""
     import torch
 
     from paper_1908_03301_gb300 import netsolve as ns
@@ -772,10 +773,11 @@ def run_fbmgen(a):
         field = torch.empty((n, n), dtype=torch.float64, device=dev)
         row = {"nodes": n * n, "log2_nodes": lg, "paper_table1_mpi_s": paper_mpi_s.get(lg)}
         for tag, cdt in (("fft_f32", torch.complex64), ("fft_f64", torch.complex128)):
-            ms_f, ms_b = [], []
+            ms_f, ms_b, ms_n = [], [], []
             for it in range(a.warmup + a.steps):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[3].record(stream)
                 noise = torch.randn((n, n), dtype=cdt, device=dev, generator=gen)
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 e[0].record(stream)
                 ns.fbm_field(dims, noise, 0.7, out=field)
                 e[1].record(stream)
@@ -783,11 +785,13 @@ def run_fbmgen(a):
                 e[2].record(stream)
                 torch.cuda.synchronize()
                 if it >= a.warmup:
+                    ms_n.append(e[3].elapsed_time(e[0]))
                     ms_f.append(e[0].elapsed_time(e[1]))
                     ms_b.append(e[1].elapsed_time(e[2]))
                 del noise, planes
             row[tag] = {"field_ms": statistics.mean(ms_f), "bonds_ms": statistics.mean(ms_b),
                         "total_ms": statistics.mean(ms_f) + statistics.mean(ms_b),
+                        "noise_draw_ms_torch": statistics.mean(ms_n),
                         "field_check": {"mean": float(field.mean()), "var": float((field * field).mean())}}
         rows.append(row)
         del field
