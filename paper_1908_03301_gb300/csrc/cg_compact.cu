@@ -3,7 +3,8 @@
 // Near the percolation threshold the unknowns of the linear system (the
 // spanning clusters less their dead-end trees) are a small part of the
 // lattice: 13 % of a 256^3 network at p = 0.26.  A sweep over the lattice
-// then moves mostly zeros.  Here the unknowns are listed in lattice order;
+// then moves mostly zeros.  Here the unknowns are listed row by row (in 3D,
+// rows in blocks of 8 x 8; see lattice_index);
 // each keeps its scaled bonds to the +e_d neighbours and the list indices of
 // its y and z neighbours (x neighbours are the adjacent list entries); the
 // table is stored direction-major, so a warp reads consecutive entries, and
@@ -53,8 +54,26 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Order of the listed unknowns: whole padded rows (so the +x neighbour of an
+// unknown, if listed, is the next entry), the rows of a 3D network taken in
+// blocks of 8 x 8 (y, z) rows.  A z neighbour is then a few rows away in the
+// list (8 inside a block) instead of a whole plane, so the gathers of the
+// operator mostly stay within the lines a CTA reads anyway.  Scan position t
+// in [0, px * ny * nz) -> padded lattice index; a bijection.
+constexpr long long ROW_BY = 8, ROW_BZ = 8;
 __device__ __forceinline__ long long lattice_index(const Geom &g, long long t) {
-    return g.pad + t;  // t runs over the padded grid (px * ny * nz), row-major
+    if (g.ndim < 3) return g.pad + t;
+    const long long rho = t / g.px;
+    const int x = (int)(t - rho * g.px);
+    const long long ny = g.ny, nz = g.nz;
+    const long long zb = rho / (ROW_BZ * ny);
+    const long long hz = nz - zb * ROW_BZ < ROW_BZ ? nz - zb * ROW_BZ : ROW_BZ;
+    const long long r1 = rho - zb * ROW_BZ * ny;
+    const long long yb = r1 / (hz * ROW_BY);
+    const long long hy = ny - yb * ROW_BY < ROW_BY ? ny - yb * ROW_BY : ROW_BY;
+    const long long r2 = r1 - yb * hz * ROW_BY;
+    const long long zz = r2 / hy, yy = r2 - zz * hy;
+    return g.idx(x, (int)(yb * ROW_BY + yy), (int)(zb * ROW_BZ + zz));
 }
 
 // ------------------------------------------------------------------ build
@@ -117,7 +136,7 @@ __global__ void compact_index_kernel(Geom g, const uint8_t *__restrict__ cls,
     }
 }
 
-// ELL row of every unknown.  In lattice order an unknown's +x neighbour, if
+// ELL row of every unknown.  In list order (whole rows) an unknown's +x neighbour, if
 // it is an unknown, is the next entry of the list, so x needs no index (x is
 // never periodic).  The y and z neighbours follow periodic boundaries.
 //   val[d][k]  (d < ndim, stride U + 1): scaled bond to the +e_d neighbour if
