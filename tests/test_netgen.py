@@ -46,3 +46,35 @@ def test_aniso_instances_are_seeded_and_distinct():
     d2, p2 = netgen.aniso_instance(0, 1, 2, n=64)
     d3, p3 = netgen.aniso_instance(0, 1, 3, n=64)
     assert d1 == (64, 64) and np.array_equal(p1[0], p2[0]) and not np.array_equal(p1[0], p3[0])
+
+
+def test_periodic_plane_shapes_and_wrap_bonds():
+    """Along a periodic axis a plane has one bond per node; the generators'
+    wrap layer joins the last node layer to the first (mean of the two end
+    nodes for the FBM map), and the other bonds equal the no-flow ones."""
+    dims = (12, 9, 7)
+    assert netgen.plane_shape(dims, 1, periodic=(1,)) == (7, 9, 12)
+    assert netgen.plane_shape(dims, 1) == (7, 8, 12)
+    assert netgen.n_bonds(dims, periodic=(1, 2)) == [11 * 9 * 7, 12 * 9 * 7, 12 * 9 * 7]
+    a = netgen.fbm_bonds(dims, 0.6, 1.0, netgen.rng(5))
+    b = netgen.fbm_bonds(dims, 0.6, 1.0, netgen.rng(5), periodic=(1, 2))
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1][:, :-1, :])
+    np.testing.assert_array_equal(a[2], b[2][:-1])
+    B = netgen.fbm_field(netgen.node_shape(dims), 0.6, netgen.rng(5))
+    np.testing.assert_allclose(b[1][:, -1, :], np.exp(0.5 * (B[:, -1, :] + B[:, 0, :])), rtol=1e-15)
+    np.testing.assert_allclose(b[2][-1], np.exp(0.5 * (B[-1] + B[0])), rtol=1e-15)
+    u = netgen.uniform(dims, 2.0, periodic=(2,))
+    assert [g.shape for g in u] == [(7, 9, 11), (7, 8, 12), (7, 9, 12)]
+
+
+def test_fbm_generator_matches_oracle_filtering():
+    """netgen's isotropic FBM field (the workloads' inputs) is the oracle's
+    spectral filtering of the same noise draw."""
+    import oracle
+
+    shape = (40, 56)
+    field = netgen.fbm_field(shape, 0.7, netgen.rng(77))
+    gen = netgen.rng(77)
+    noise = gen.standard_normal(shape) + 1j * gen.standard_normal(shape)
+    np.testing.assert_allclose(field, oracle.fbm_field(noise, 0.7), rtol=0, atol=1e-12)
