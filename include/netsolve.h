@@ -255,11 +255,15 @@ net_status net_destroy(net_t *net);
  *   label   device output, N int32 (may be NULL); cls: device output, N uint8
  *           (may be NULL).  N = nx*ny*nz.
  * The union-find scratch is a fixed array inside the library's device image,
- * sized for NET_NOALLOC_MAX_NODES nodes (8 MiB); every GPU that loads the
- * library holds it until the process exits.  N above that limit returns
- * NET_EINVAL.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array, so
+ * sized for NET_NOALLOC_MAX_NODES nodes (8 MiB); once the library's device
+ * code is loaded on a GPU, that GPU holds it until the process exits.  N
+ * above that limit returns NET_EINVAL.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current.  Under lazy module loading (the CUDA default) that lookup is also
+ * what loads the device code and so creates the array: the first call on a
+ * device may allocate those 8 MiB and block.  A caller that must not allocate
+ * later makes one call at start-up (any small network will do), before its
+ * own memory pool reserves the device and before any stream capture.  All calls on a device share the array, so
  * calls that overlap on the GPU (other streams or threads) race: keep them
  * ordered.  The call returns after the work on desc->stream has finished;
  * NET_EINVAL also for a negative, NaN or infinite conductance.

@@ -44,7 +44,7 @@ cudaError_t launch_unpack_x(const Geom &g, const double *x, double *dst, cudaStr
 cudaError_t launch_unpack_labels(const Geom &g, const int *parent, const uint8_t *cls,
                                  int *label, uint8_t *cls_out, cudaStream_t st);
 
-// ---- solve (kernels_cg.cu) -------------------------------------------------
+// ---- inner CG vectors of a lattice network (one set per inner precision) ---
 struct InnerArgs {
     Geom g;
     const void *gs[3];  // scaled bonds (T)
@@ -53,9 +53,6 @@ struct InnerArgs {
     InnerScal *s;
     double *partials;
 };
-// Number of CTAs the inner iteration kernel uses for this geometry.
-int inner_grid_blocks(const Geom &g, int f32);
-cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st);
 
 // ---- whole inner solve of a 2D network in one launch (cg_persist.cu) ------
 struct PersistArgs {

@@ -1,32 +1,29 @@
-// kernels_cg.cu -- the conjugate-gradient hot loop (Sec. IV) and the FP64
-// residual pass of the iterative refinement.
+// kernels_cg.cu -- the FP64 side of the iterative refinement (Sec. IV): the
+// correction update, the true-residual pass and the arming of the next inner
+// CG solve.
 //
-// Inner loop.  Jacobi preconditioning is applied as the symmetric scaling
+// The inner CG iteration itself runs in cg_persist.cu (2D, FP32, one
+// cooperative launch per inner solve), sweep.cu (one launch per iteration
+// over a planned list of segments) and cg_compact.cu (listed unknowns).  All
+// three apply Jacobi preconditioning as the symmetric scaling
 // A = D^-1/2 G D^-1/2 (unit diagonal), so preconditioned CG on G becomes
-// plain CG on A and the iteration reads no diagonal.  One kernel launch is
-// one full CG iteration.  Launch k
-//   1. finishes iteration k-1 from its scalars alpha, beta:
+// plain CG on A and the iteration reads no diagonal, and all three compute one
+// iteration in one pass over the data:
+//   1. finish iteration k-1 from its scalars alpha, beta:
 //        r_k = r_{k-1} - alpha q_{k-1},  p_k = r_k + beta p_{k-1},
-//        y_k = y_{k-1} + alpha p_{k-1},
-//      for its tile and (p only) a one-node halo, staged in shared memory;
-//   2. computes q_k = A p_k from the staged p_k (5- or 7-point stencil on
-//      the bond planes) and the four sums <p,q>, <r,q>, <q,q>, <r,r>;
-//   3. the last CTA to finish reduces the sums (grid_reduce) and sets
+//        y_k = y_{k-1} + alpha p_{k-1};
+//   2. q_k = A p_k (5- or 7-point stencil on the bond planes) and the four
+//      sums <p,q>, <r,q>, <q,q>, <r,r>;
+//   3. one grid-wide reduction, then
 //        alpha_k = <r,r> / <p,q>,
 //        beta_k  = <r_{k+1}, r_{k+1}> / <r,r>   with
 //        <r_{k+1}, r_{k+1}> = <r,r> - 2 alpha_k <r,q> + alpha_k^2 <q,q>,
-//      the expansion of ||r_k - alpha_k q_k||^2, so one reduction per
-//      iteration suffices.
-// Every vector is read once and written once per iteration:
-// y, r, p, q (4 + 4 accesses) plus one bond plane per dimension, the
-// 32 + 4d bytes per unknown of the FP32 path.  r, p and q are double
-// buffered (iteration k reads set k%2 and writes the other), so a CTA can
-// read its neighbours' previous values for the halo while they write.  The paper's three kernels per
-// iteration with a host-side final sum (Sec. IV) become one kernel with an
-// on-device reduction.
+//      the expansion of ||r_k - alpha_k q_k||^2.
+// The paper's three kernels per iteration with a host-side final sum
+// (Sec. IV) become one pass with an on-device reduction.
 //
-// Outer loop (FP64).  One launch applies the previous correction
-// x += D^-1/2 y (tile + halo), recomputes the true residual
+// Outer loop (FP64, this file).  correct_kernel applies the previous
+// correction x += D^-1/2 y; outer_kernel then recomputes the true residual
 // r = b - G x = sum_j g_ij (x_j - x_i) at interior nodes with the raw bonds,
 // writes the scaled residual D^-1/2 r as the next inner right-hand side, and
 // reduces ||r||^2, max |r|, the face flows Q_in / Q_out (Eq. 4) and the
@@ -40,198 +37,6 @@ namespace netsolve {
 namespace {
 
 constexpr int NT = 256;
-
-// p_new = (r - alpha q) + beta p, identical on the owner and in every halo.
-template <typename T>
-__device__ __forceinline__ T rnew(T r, T q, T alpha) { return fma(-alpha, q, r); }
-template <typename T>
-__device__ __forceinline__ T pnew(T rn, T p, T beta) { return fma(beta, p, rn); }
-
-template <typename T, int NDIM, int TW, int TH, int TD>
-struct Tile {
-    static constexpr int V = Vec<T>::N;
-    static constexpr int TX = TW / V;                 // vector columns
-    static constexpr int ZP = NDIM == 3 ? TD + 2 : 1; // staged planes
-    static constexpr int ZO = NDIM == 3 ? 1 : 0;
-    static constexpr int SH = TH + 2;
-    static constexpr int SW = TW + 2 * V;             // staged row width
-    static constexpr int ITEMS = TX * TH * TD / NT;
-    static constexpr int HY = 2 * TD * TX;            // row-halo vectors
-    static constexpr int HZ = NDIM == 3 ? 2 * TH * TX : 0;
-    static constexpr int HX = 2 * TH * TD;            // column-halo scalars
-    static_assert(TW % V == 0, "tile width");
-    static_assert((TX * TH * TD) % NT == 0, "tile size must be a multiple of the CTA");
-    static_assert(NDIM == 3 || TD == 1, "2D tiles are one plane");
-    __device__ static int sidx(int zz, int yy, int xx) { return (zz * SH + yy) * SW + V + xx; }
-};
-
-template <typename T, int NDIM, int TW, int TH, int TD>
-__global__ void __launch_bounds__(NT)
-inner_iter_kernel(Geom g, const T *__restrict__ g0, const T *__restrict__ g1,
-                  const T *__restrict__ g2, T *__restrict__ y, T *r0, T *r1, T *p0, T *p1,
-                  T *q0, T *q1, InnerScal *s, double *partials) {
-    using TL = Tile<T, NDIM, TW, TH, TD>;
-    constexpr int V = TL::V;
-    __shared__ __align__(16) T sp[TL::ZP * TL::SH * TL::SW];
-
-    if (*(volatile int *)&s->stop) return;
-    const long long iter = s->iter;
-    const bool first = (iter == 0);
-    const T alpha = (T)s->alpha, beta = (T)s->beta;
-    // r, p, q are double-buffered: neighbours read the previous values as
-    // halo while the owner writes the new ones.  Iteration k reads set k%2.
-    const bool odd = iter & 1;
-    const T *__restrict__ r = odd ? r1 : r0;
-    const T *__restrict__ p = odd ? p1 : p0;
-    const T *__restrict__ q = odd ? q1 : q0;
-    T *__restrict__ ro = odd ? r0 : r1;
-    T *__restrict__ po = odd ? p0 : p1;
-    T *__restrict__ qo = odd ? q0 : q1;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, z0 = blockIdx.z * TD;
-
-    // ---- 1. finish the previous iteration on the tile, stage p_k ----------
-    Vec<T> rn[TL::ITEMS];
-#pragma unroll
-    for (int it = 0; it < TL::ITEMS; it++) {
-        const int item = threadIdx.x + it * NT;
-        const int vx = item % TL::TX, t = item / TL::TX, yy = t % TH, zz = t / TH;
-        const int x = x0 + vx * V, yq = y0 + yy, z = z0 + zz;
-        Vec<T> pn;
-        if (x < g.px && yq < g.ny && z < g.nz) {
-            const long long i = g.idx(x, yq, z);
-            Vec<T> rv;
-            rv.load(r + i);
-            if (first) {
-                rn[it] = rv;
-                pn = rv;
-                Vec<T> zv;
-                zv.zero();
-                zv.store(y + i);
-                rv.store(ro + i);
-            } else {
-                Vec<T> qv, pv, yv;
-                qv.load(q + i);
-                pv.load(p + i);
-                yv.load(y + i);
-#pragma unroll
-                for (int k = 0; k < V; k++) {
-                    rn[it].v[k] = rnew(rv.v[k], qv.v[k], alpha);
-                    pn.v[k] = pnew(rn[it].v[k], pv.v[k], beta);
-                    yv.v[k] = fma(alpha, pv.v[k], yv.v[k]);
-                }
-                rn[it].store(ro + i);
-                yv.store(y + i);
-            }
-            pn.store(po + i);
-        } else {
-            rn[it].zero();
-            pn.zero();
-        }
-        pn.store(sp + TL::sidx(zz + TL::ZO, yy + 1, vx * V));
-    }
-    // halo rows (and planes in 3D): p only
-    for (int item = threadIdx.x; item < TL::HY + TL::HZ; item += NT) {
-        int vx, yy, zz;
-        if (item < TL::HY) {
-            vx = item % TL::TX;
-            const int t = item / TL::TX;
-            zz = t % TD;
-            yy = (t / TD) ? TH : -1;
-        } else {
-            const int i2 = item - TL::HY;
-            vx = i2 % TL::TX;
-            const int t = i2 / TL::TX;
-            yy = t % TH;
-            zz = (t / TH) ? TD : -1;
-        }
-        const int x = x0 + vx * V, yq = y0 + yy, z = z0 + zz;
-        Vec<T> pn;
-        if (x < g.px && yq >= 0 && yq < g.ny && z >= 0 && z < g.nz) {
-            const long long i = g.idx(x, yq, z);
-            Vec<T> rv;
-            rv.load(r + i);
-            if (first) {
-                pn = rv;
-            } else {
-                Vec<T> qv, pv;
-                qv.load(q + i);
-                pv.load(p + i);
-#pragma unroll
-                for (int k = 0; k < V; k++) pn.v[k] = pnew(rnew(rv.v[k], qv.v[k], alpha), pv.v[k], beta);
-            }
-        } else {
-            pn.zero();
-        }
-        pn.store(sp + TL::sidx(zz + TL::ZO, yy + 1, vx * V));
-    }
-    // halo columns: scalars
-    for (int item = threadIdx.x; item < TL::HX; item += NT) {
-        const int side = item & 1, t = item >> 1, yy = t % TH, zz = t / TH;
-        const int x = side ? x0 + TW : x0 - 1, yq = y0 + yy, z = z0 + zz;
-        T pn = T(0);
-        if (x >= 0 && x < g.px && yq < g.ny && z < g.nz) {
-            const long long i = g.idx(x, yq, z);
-            pn = first ? r[i] : pnew(rnew(r[i], q[i], alpha), p[i], beta);
-        }
-        sp[TL::sidx(zz + TL::ZO, yy + 1, side ? TW : -1)] = pn;
-    }
-    __syncthreads();
-
-    // ---- 2. q = A p on the tile and the four sums -----------------------
-    T a_pq = T(0), a_rq = T(0), a_qq = T(0), a_rr = T(0);
-#pragma unroll
-    for (int it = 0; it < TL::ITEMS; it++) {
-        const int item = threadIdx.x + it * NT;
-        const int vx = item % TL::TX, t = item / TL::TX, yy = t % TH, zz = t / TH;
-        const int x = x0 + vx * V, yq = y0 + yy, z = z0 + zz;
-        if (!(x < g.px && yq < g.ny && z < g.nz)) continue;
-        const long long i = g.idx(x, yq, z);
-        const T *row = sp + TL::sidx(zz + TL::ZO, yy + 1, vx * V);
-        Vec<T> pc, pu, pd, gx, gy, gym, qv;
-        pc.load(row);
-        pu.load(row + TL::SW);
-        pd.load(row - TL::SW);
-        const T pl = row[-1], pr = row[V];
-        gx.load(g0 + i);
-        const T gxm = g0[i - 1];
-        gy.load(g1 + i);
-        gym.load(g1 + i - g.px);
-        Vec<T> pf, pb, gz, gzm;
-        if (NDIM == 3) {
-            pf.load(row + TL::SH * TL::SW);
-            pb.load(row - TL::SH * TL::SW);
-            gz.load(g2 + i);
-            gzm.load(g2 + i - g.plane);
-        }
-#pragma unroll
-        for (int k = 0; k < V; k++) {
-            const T left = k == 0 ? pl : pc.v[k - 1];
-            const T right = k == V - 1 ? pr : pc.v[k + 1];
-            const T gl = k == 0 ? gxm : gx.v[k - 1];
-            T nb = gl * left;
-            nb = fma(gx.v[k], right, nb);
-            nb = fma(gym.v[k], pd.v[k], nb);
-            nb = fma(gy.v[k], pu.v[k], nb);
-            if (NDIM == 3) {
-                nb = fma(gzm.v[k], pb.v[k], nb);
-                nb = fma(gz.v[k], pf.v[k], nb);
-            }
-            const T qk = pc.v[k] - nb;
-            qv.v[k] = qk;
-            a_pq = fma(pc.v[k], qk, a_pq);
-            a_rq = fma(rn[it].v[k], qk, a_rq);
-            a_qq = fma(qk, qk, a_qq);
-            a_rr = fma(rn[it].v[k], rn[it].v[k], a_rr);
-        }
-        qv.store(qo + i);
-    }
-
-    // ---- 3. one grid reduction; the last CTA sets the next step ----------
-    double v[4] = {(double)a_pq, (double)a_rq, (double)a_qq, (double)a_rr};
-    const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM};
-    if (!grid_reduce<4, NT>(v, ops, partials, &s->counter)) return;
-    if (threadIdx.x == 0) finish_iteration(s, iter, v);
-}
 
 // ---------------------------------------------------------------------------
 // outer FP64 residual pass (scalar per node; runs a few times per solve)
@@ -405,32 +210,6 @@ outer_kernel(Geom g, const GT *__restrict__ g0, const GT *__restrict__ g1,
     is->stop = (v[2] > 0.0 && !done) ? 0 : 1;
 }
 
-// ---------------------------------------------------------------------------
-// tile configurations
-// ---------------------------------------------------------------------------
-template <typename T, int NDIM> struct InnerCfg;
-template <> struct InnerCfg<float, 2> { static constexpr int TW = 256, TH = 16, TD = 1; };
-template <> struct InnerCfg<double, 2> { static constexpr int TW = 128, TH = 16, TD = 1; };
-template <> struct InnerCfg<float, 3> { static constexpr int TW = 64, TH = 8, TD = 8; };
-template <> struct InnerCfg<double, 3> { static constexpr int TW = 32, TH = 8, TD = 8; };
-
-template <typename T, int NDIM>
-dim3 inner_grid(const Geom &g) {
-    using C = InnerCfg<T, NDIM>;
-    return dim3((g.px + C::TW - 1) / C::TW, (g.ny + C::TH - 1) / C::TH,
-                NDIM == 3 ? (g.nz + C::TD - 1) / C::TD : 1);
-}
-
-template <typename T, int NDIM>
-cudaError_t launch_inner_t(const InnerArgs &a, cudaStream_t st) {
-    using C = InnerCfg<T, NDIM>;
-    inner_iter_kernel<T, NDIM, C::TW, C::TH, C::TD><<<inner_grid<T, NDIM>(a.g), NT, 0, st>>>(
-        a.g, (const T *)a.gs[0], (const T *)a.gs[1], (const T *)a.gs[2], (T *)a.y,
-        (T *)a.r[0], (T *)a.r[1], (T *)a.p[0], (T *)a.p[1], (T *)a.q[0], (T *)a.q[1], a.s,
-        a.partials);
-    return cudaGetLastError();
-}
-
 template <int NDIM>
 dim3 outer_grid(const Geom &g) {
     using OT = OTile<NDIM>;
@@ -450,16 +229,6 @@ cudaError_t launch_outer_t(const OuterArgs &a, cudaStream_t st) {
 inline long long nblocks(dim3 d) { return (long long)d.x * d.y * d.z; }
 
 }  // namespace
-
-int inner_grid_blocks(const Geom &g, int f32) {
-    if (g.ndim == 2) return (int)nblocks(f32 ? inner_grid<float, 2>(g) : inner_grid<double, 2>(g));
-    return (int)nblocks(f32 ? inner_grid<float, 3>(g) : inner_grid<double, 3>(g));
-}
-
-cudaError_t launch_inner_iter(const InnerArgs &a, int f32, cudaStream_t st) {
-    if (a.g.ndim == 2) return f32 ? launch_inner_t<float, 2>(a, st) : launch_inner_t<double, 2>(a, st);
-    return f32 ? launch_inner_t<float, 3>(a, st) : launch_inner_t<double, 3>(a, st);
-}
 
 int outer_grid_blocks(const Geom &g) {
     return (int)(g.ndim == 2 ? nblocks(outer_grid<2>(g)) : nblocks(outer_grid<3>(g)));

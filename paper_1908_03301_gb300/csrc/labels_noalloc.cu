@@ -8,12 +8,17 @@
 // the bond planes and the two output arrays, and the union-find scratch lives
 // in one fixed array of device memory that is part of the library image.
 //
-// That array, g_scratch, is a static __device__ object of a fixed size: every
-// GPU that loads the library holds it until the process exits, and all calls
-// on one device share it.  Host code cannot use the name g_scratch as a device
-// address; the device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made on that device) and passed to
-// the kernels.  Calls that overlap on the GPU (two streams, or two threads)
+// That array, g_scratch, is a static __device__ object of a fixed size: once
+// the library's device code is loaded on a GPU, that GPU holds it until the
+// process exits, and all calls on one device share it.  Under lazy module
+// loading (the CUDA default) the device code, and with it the array, is
+// loaded on its first use on a device, which here is the address lookup of
+// the first call: that first call can therefore allocate the array's memory
+// and block, so a caller that may not allocate later makes one call at
+// start-up, before its own pool takes the device memory.  Host code cannot use
+// the name g_scratch as a device address; the device address is looked up
+// once per device with cudaGetSymbolAddress (on the first call made on that
+// device) and passed to the kernels.  Calls that overlap on the GPU (two streams, or two threads)
 // would race on the shared array; the entry point serialises nothing, so the
 // caller must keep calls on one device ordered.
 //

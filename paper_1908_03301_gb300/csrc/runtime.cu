@@ -191,13 +191,6 @@ net_status netsolve::ensure_precision(net_t *n, int f32, cudaStream_t st) {
 
 namespace {
 
-// NETSOLVE_KERNEL selects the inner-loop kernel for comparisons:
-// "persist" (default where it applies), "sweep" or "tiled".
-bool use_sweep_kernel() {
-    const char *e = getenv("NETSOLVE_KERNEL");
-    return !(e && strcmp(e, "tiled") == 0);
-}
-
 // The compacted solve replaces the lattice kernels when the unknowns are a
 // small part of the lattice (its list traffic is about twice a lattice
 // sweep's per node): below 35 % of the lattice nodes, or always with
@@ -221,7 +214,7 @@ bool use_persist_kernel(const net_t *n, int f32) {
     if (use_compact_kernel(n, f32)) return false;
     if (n->g.per) return persist_applies(n->g, f32);
     const char *e = getenv("NETSOLVE_KERNEL");
-    if (e && (strcmp(e, "tiled") == 0 || strcmp(e, "sweep") == 0 || strcmp(e, "compact") == 0)) return false;
+    if (e && (strcmp(e, "sweep") == 0 || strcmp(e, "compact") == 0)) return false;
     return persist_applies(n->g, f32);
 }
 
@@ -344,32 +337,25 @@ net_status sweep_shape_for(net_t *n, int f32, PlanShape *shape) {
 
 net_status ensure_graph(net_t *n, int f32, int K) {
     const int k = f32 ? 0 : 1;
-    const bool sweep = use_sweep_kernel();
     PlanShape shape;
-    if (sweep) {
-        net_status s = sweep_shape_for(n, f32, &shape);
-        if (s != NET_OK) return s;
-    }
-    if (n->gexec[k] && n->gk[k] == K && (!sweep || (n->sw[k].segs && same_shape(n->sw[k].shape, shape))))
+    net_status s = sweep_shape_for(n, f32, &shape);
+    if (s != NET_OK) return s;
+    if (n->gexec[k] && n->gk[k] == K && n->sw[k].segs && same_shape(n->sw[k].shape, shape))
         return NET_OK;
     if (n->gexec[k]) {
         cudaGraphExecDestroy(n->gexec[k]);
         n->gexec[k] = nullptr;
     }
-    InnerArgs a = inner_args(n, f32);
-    if (sweep) {
-        net_status s = ensure_sweep_plan(n, f32, shape);
-        if (s != NET_OK) return s;
-        CK(sweep_prepare(n->g.ndim, f32));
-    }
+    s = ensure_sweep_plan(n, f32, shape);
+    if (s != NET_OK) return s;
+    CK(sweep_prepare(n->g.ndim, f32));
     const SweepDev &sd = n->sw[k];
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     for (int i = 0; e == cudaSuccess && i < K; i++)
-        e = sweep ? launch_sweep(n->g.ndim, f32, sd.grid, sd.inst, sd.segs, sd.cta, cs)
-                  : launch_inner_iter(a, f32, cs);
+        e = launch_sweep(n->g.ndim, f32, sd.grid, sd.inst, sd.segs, sd.cta, cs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&n->gexec[k], graph, 0);
@@ -599,8 +585,7 @@ net_status setup_network(net_t *n, const void *const g[3], int on_device) {
     CK(dalloc(&n->dis, L * 8, st));
     CK(dalloc(&n->x, L * 8, st));
     const long long nb = std::max<long long>(
-        {(long long)inner_grid_blocks(G, 1), (long long)inner_grid_blocks(G, 0),
-         (long long)outer_grid_blocks(G), 152LL * 16});
+        {(long long)outer_grid_blocks(G), 152LL * 16});
     CK(dalloc(&n->partials, (size_t)nb * 8 * sizeof(double), st));
     CK(dalloc(&n->dsc, sizeof(DevScal), st));
     unsigned int *flags = nullptr;

@@ -251,14 +251,14 @@ def _ill_conditioned(dims, seed):
 
 @pytest.mark.parametrize("refine", [0, 1])
 @pytest.mark.parametrize("kernel,dims", [("persist", (150, 131)), ("sweep", (150, 131)),
-                                         ("tiled", (150, 131)), ("sweep", (23, 30, 27)),
-                                         ("tiled", (23, 30, 27))])
+                                         ("compact", (150, 131)), ("sweep", (23, 30, 27)),
+                                         ("compact", (23, 30, 27))])
 def test_refine_modes_every_kernel(ns, kernel_env, kernel, dims, refine):
     """Reliable updates (the recursion kept across refinement passes, with
     the true residual put in place of the recursive one) and classical
     restarted refinement reach the oracle's G_eff and pressures through each
     inner-loop kernel: the persistent in-place kernel, the double-buffered
-    sweep kernel and the tiled kernel."""
+    sweep kernel and the compacted solve."""
     kernel_env["NETSOLVE_KERNEL"] = kernel
     planes = _ill_conditioned(dims, 40 + len(dims))
     ref = oracle.solve(dims, planes, tol=1e-13)
