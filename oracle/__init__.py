@@ -5,5 +5,5 @@ and reference legs may import this package.  The CUDA solver never does.
 """
 from .oracle import (  # noqa: F401
     CLS_FACE_IN, CLS_FACE_OUT, CLS_INLET, CLS_ISOLATED, CLS_OUTLET, CLS_SPANNING,
-    backbone, build, close_smallest, fbm_bonds, fbm_field, labels, max_threads, residual, solve,
+    backbone, backbone_blocks, build, close_smallest, fbm_bonds, fbm_field, labels, max_threads, residual, solve,
 )

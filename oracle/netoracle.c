@@ -280,6 +280,137 @@ out:
     return rc;
 }
 
+/*
+ * Current-carrying backbone (Sec. V and VI.B: near the percolation threshold
+ * most of the spanning cluster carries no flow).  The graph: the interior
+ * nodes joined by their open bonds; all inlet-face nodes taken together as
+ * one vertex A and all outlet-face nodes as one vertex B (each face is at one
+ * pressure, so it acts as one node); and one extra edge joining A and B.
+ * For generic conductances a bond carries current exactly when it lies on a
+ * path from A to B that visits no vertex twice, which is exactly when it
+ * belongs to the same biconnected component (block) as the extra edge A-B.
+ * Every other part of a spanning cluster hangs from that block by a single
+ * node (a dead-end tree, or a dead-end loop), or by one face.
+ *
+ * The blocks come from one depth-first search (Hopcroft and Tarjan 1973):
+ * disc[v] is v's discovery time, low[v] the smallest discovery time reachable
+ * from v's subtree by one edge that is not a tree edge; edges are pushed on a
+ * stack as they are met, and when the search returns from a child w of v with
+ * low[w] >= disc[v] the edges above (v, w) on the stack, (v, w) included, are
+ * one block.  The lattice has no parallel edges (periodic axes have at least
+ * three nodes, and n_f >= 3 keeps the faces apart), so the tree edge to a
+ * node's parent is recognised by the parent vertex.
+ *
+ * backbone[i] = 1 for the interior nodes that are an end of an edge of the
+ * block of A-B, 0 for every other node.  Returns 0, or -1 on bad input.
+ */
+static int faces_kind(const or_desc *d, int64_t j) {
+    int64_t c[3];
+    coords(d, j, c);
+    return node_kind(d, c);
+}
+
+int or_backbone_blocks(const or_desc *d, const double *const g[3], uint8_t *backbone) {
+    if (validate(d, g)) return -1;
+    const int64_t N = n_nodes(d), A = N, B = N + 1, V = N + 2;
+    const int nk = 2 * d->ndim;
+    int64_t *disc = (int64_t *)calloc((size_t)V, sizeof(int64_t));
+    int64_t *low = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+    int64_t *par = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+    int64_t *nxt = (int64_t *)calloc((size_t)V, sizeof(int64_t));   /* next neighbour slot */
+    int64_t *adjA = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    int64_t *adjB = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    int64_t *dstack = (int64_t *)malloc(sizeof(int64_t) * (size_t)V); /* DFS path */
+    int64_t ne_max = (int64_t)d->ndim * N + 2 * N + 1;
+    int64_t *eu = (int64_t *)malloc(sizeof(int64_t) * (size_t)ne_max);  /* edge stack */
+    int64_t *ew = (int64_t *)malloc(sizeof(int64_t) * (size_t)ne_max);
+    int rc = -1;
+    if (!disc || !low || !par || !nxt || !adjA || !adjB || !dstack || !eu || !ew) goto out;
+    memset(backbone, 0, (size_t)N);
+
+    /* neighbours of the two face vertices: the interior nodes with an open
+     * bond to that face, in index order (slot 0 of each is the other face) */
+    int64_t nA = 0, nB = 0;
+    for (int64_t i = 0; i < N; i++) {
+        int64_t c[3], j;
+        double gij;
+        coords(d, i, c);
+        if (node_kind(d, c) != 0) continue;
+        for (int k = 0; k < nk; k++) {
+            if (!neighbour(d, g, c, k, &j, &gij) || !(gij > 0.0)) continue;
+            int kj = faces_kind(d, j);
+            if (kj == 1) adjA[nA++] = i;
+            if (kj == 2) adjB[nB++] = i;
+        }
+    }
+
+    int64_t time = 0, top = 0, etop = 0;
+    disc[A] = low[A] = ++time;
+    par[A] = -1;
+    dstack[top++] = A;
+    while (top > 0) {
+        const int64_t v = dstack[top - 1];
+        /* next neighbour w of v, or -1 when v is done */
+        int64_t w = -1;
+        while (w < 0) {
+            const int64_t slot = nxt[v]++;
+            if (v == A || v == B) {
+                const int64_t *adj = v == A ? adjA : adjB;
+                const int64_t na = v == A ? nA : nB;
+                if (slot == 0) w = v == A ? B : A;
+                else if (slot <= na) w = adj[slot - 1];
+                else break;
+            } else {
+                if (slot >= nk) break;
+                int64_t c[3], j;
+                double gij;
+                coords(d, v, c);
+                if (!neighbour(d, g, c, (int)slot, &j, &gij) || !(gij > 0.0)) continue;
+                int kj = faces_kind(d, j);
+                w = kj == 1 ? A : kj == 2 ? B : j;
+            }
+        }
+        if (w >= 0) {
+            if (w == par[v]) continue;
+            if (disc[w] == 0) {             /* tree edge: descend */
+                eu[etop] = v; ew[etop] = w; etop++;
+                par[w] = v;
+                disc[w] = low[w] = ++time;
+                dstack[top++] = w;
+            } else if (disc[w] < disc[v]) { /* edge back to an ancestor */
+                eu[etop] = v; ew[etop] = w; etop++;
+                if (disc[w] < low[v]) low[v] = disc[w];
+            }
+            continue;
+        }
+        /* v is finished: return to its parent u */
+        top--;
+        const int64_t u = par[v];
+        if (u < 0) break;
+        if (low[v] < low[u]) low[u] = low[v];
+        if (low[v] >= disc[u]) {
+            /* the edges above (u, v) on the stack form one block */
+            int64_t e = etop;
+            int has_ab = 0;
+            do {
+                e--;
+                if ((eu[e] == A && ew[e] == B) || (eu[e] == B && ew[e] == A)) has_ab = 1;
+            } while (!(eu[e] == u && ew[e] == v));
+            if (has_ab)
+                for (int64_t k = e; k < etop; k++) {
+                    if (eu[k] < N) backbone[eu[k]] = 1;
+                    if (ew[k] < N) backbone[ew[k]] = 1;
+                }
+            etop = e;
+        }
+    }
+    rc = 0;
+out:
+    free(disc); free(low); free(par); free(nxt); free(adjA); free(adjB);
+    free(dstack); free(eu); free(ew);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* vector helpers (fixed-order sums)                                   */
 /* ------------------------------------------------------------------ */

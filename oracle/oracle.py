@@ -78,6 +78,8 @@ def _load():
         lib.or_labels.restype = C.c_int
         lib.or_backbone.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p]
         lib.or_backbone.restype = C.c_int
+        lib.or_backbone_blocks.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p]
+        lib.or_backbone_blocks.restype = C.c_int
         lib.or_residual.argtypes = [C.POINTER(_Desc), dp3, C.c_void_p, C.c_void_p]
         lib.or_residual.restype = C.c_int
         lib.or_solve.argtypes = [C.POINTER(_Desc), dp3, C.c_double, C.c_int64, C.c_int,
@@ -138,6 +140,20 @@ def backbone(dims, planes, flow_axis=0, periodic=()):
     desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0, periodic)
     out = np.empty(N, np.uint8)
     if lib.or_backbone(C.byref(desc), ptrs, out.ctypes.data) != 0:
+        raise ValueError("invalid network")
+    return out.reshape(shape).astype(bool)
+
+
+def backbone_blocks(dims, planes, flow_axis=0, periodic=()):
+    """Current-carrying backbone (bool, node-shaped): the interior nodes of
+    the biconnected component that holds the extra edge between the two faces
+    (each face taken as one vertex) -- the nodes on a path from the inlet face
+    to the outlet face that visits no node twice.  Dead-end trees and dead-end
+    loops are both left out."""
+    lib = _load()
+    desc, ptrs, keep, N, shape = _prep(dims, planes, flow_axis, 1.0, 0.0, periodic)
+    out = np.empty(N, np.uint8)
+    if lib.or_backbone_blocks(C.byref(desc), ptrs, out.ctypes.data) != 0:
         raise ValueError("invalid network")
     return out.reshape(shape).astype(bool)
 

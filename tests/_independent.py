@@ -137,3 +137,55 @@ def read_golden(path):
     dims = tuple(int(v) for v in vals["dims"])
     planes = [np.array(vals[k]) for k in ("gx", "gy", "gz")[: len(dims)]]
     return dims, planes, vals
+
+
+def contracted_graph(dims, planes, flow_axis=0, periodic=()):
+    """Adjacency sets of the open-bond graph with every inlet-face node taken
+    as the one vertex 'A' and every outlet-face node as 'B' (bonds inside a
+    face dropped)."""
+    kind = face_kind(dims, flow_axis)
+    name = {1: "A", 2: "B"}
+    adj = {}
+    for i, j, g in bond_list(dims, planes, periodic):
+        if not g > 0:
+            continue
+        u = name.get(int(kind[i]), i)
+        v = name.get(int(kind[j]), j)
+        if u == v or (isinstance(u, str) and isinstance(v, str)):
+            continue
+        adj.setdefault(u, set()).add(v)
+        adj.setdefault(v, set()).add(u)
+    return adj
+
+
+def simple_path_nodes(dims, planes, flow_axis=0, periodic=(), limit=2_000_000):
+    """Brute force over every path from 'A' to 'B' that visits no vertex twice
+    (tiny networks only): the set of interior nodes lying on at least one.
+    Bonds on such paths are the ones that carry current for generic
+    conductances."""
+    adj = contracted_graph(dims, planes, flow_axis, periodic)
+    on = set()
+    if "A" not in adj or "B" not in adj:
+        return on
+    count = 0
+    path = ["A"]
+    seen = {"A"}
+    stack = [iter(sorted(adj["A"], key=str))]
+    while stack:
+        nxt = next(stack[-1], None)
+        if nxt is None:
+            stack.pop()
+            seen.discard(path.pop())
+            continue
+        if nxt in seen:
+            continue
+        if nxt == "B":
+            on.update(v for v in path if not isinstance(v, str))
+            count += 1
+            if count > limit:
+                raise RuntimeError("too many paths for a brute-force check")
+            continue
+        path.append(nxt)
+        seen.add(nxt)
+        stack.append(iter(sorted(adj.get(nxt, ()), key=str)))
+    return on
