@@ -43,6 +43,9 @@ def args_():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the 256^3 percolation, batch and serve "
+                         "measurements that the default run adds to its line")
     ap.add_argument("--workload", default="fbm2048",
                     choices=["fbm2048", "perc3d", "batch", "serve", "aniso", "periodic", "corrperc",
                              "fbmgen"],
@@ -144,6 +147,15 @@ def profiled_traffic(kernel_hash):
     if d.get("kernel_source_hash") != kernel_hash:
         return None
     return d.get("dram_bytes_per_iteration")
+
+
+def measured_hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else
+    the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
 
 
 def stored_oracle(name):
@@ -303,12 +315,10 @@ def run_ours(a, rank, world, local):
     b_alg = 32 + 4 * d  # bytes per active unknown per FP32 inner iteration
     inner_s = r0.inner_ms / 1e3
     achieved = b_alg * r0.n_active * r0.inner_iters / inner_s / 1e9 if inner_s > 0 else None
-    peaks_p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_p):
-        peak, peak_src = float(json.load(open(peaks_p))["hbm_gbs"]), "measured"
+    peak, peak_src = measured_hbm_peak()
     khash = kernel_source_hash()
     traffic = profiled_traffic(khash)
+    dram_gbs = traffic * r0.inner_iters / inner_s / 1e9 if (traffic and inner_s > 0) else None
     ref = stored_oracle("fbm2048_iso_x") if a.size == 2048 else None
     rel_vs_oracle = abs(r0.g_eff - ref["g_eff"]) / ref["g_eff"] if ref else None
     rel64 = abs(res64[-1].g_eff - ref["g_eff"]) / ref["g_eff"] if (ref and res64) else None
@@ -334,17 +344,37 @@ def run_ours(a, rank, world, local):
                      "g_eff": res64[-1].g_eff, "rel_err_vs_oracle": rel64,
                      "speedup_mixed_over_fp64": statistics.mean(ms64) / statistics.mean(ms)}
                     if ms64 else None),
-        "cg_hbm_gbs": achieved,
+        "cg_algorithmic_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "cg_persist_kernel (one CG iteration = one unit)",
                      "peak_source": peak_src, "bytes_per_unknown_iter": b_alg,
-                     "algorithmic_bytes_per_iteration": b_alg * r0.n_active},
+                     "algorithmic_bytes_per_iteration": b_alg * r0.n_active,
+                     "dram_gbs": dram_gbs, "dram_frac": (dram_gbs / peak) if dram_gbs else None,
+                     "note": "achieved = algorithmic bytes (40 B x unknowns) per iteration / time per "
+                             "iteration; y, r, p and q stay in an L2 set-aside during the solve, so "
+                             "DRAM carries only `traffic` bytes per iteration (ncu, same kernel "
+                             "source): dram_gbs = traffic / time per iteration"},
         "e2e": ({"value": len(e2e_t) / sum(e2e_t), "unit": "solves/s",
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h} if e2e_t else None),
         "gpu_launches": int(launches * a.steps),
         "clocks": clocks,
     }
+    if world == 1 and not a.no_extra:
+        # the other workloads, each under its own clock record
+        line["configs"] = {}
+        for name, fn in (("perc3d", lambda: perc3d_line(a, 3, 1, 1)),
+                         ("batch", lambda: batch_line(a, 0, 1, local, 1, 1)),
+                         ("serve", lambda: serve_line(a, 400, (0.5,), 150))):
+            t = time.perf_counter()
+            try:
+                sub = fn()
+            except Exception as e:  # reported, the headline stands
+                sub = {"error": f"{type(e).__name__}: {e}"}
+            if isinstance(sub, dict):
+                sub.pop("metric", None)
+                sub["bench_wall_s"] = time.perf_counter() - t
+            line["configs"][name] = sub
     if world == 1 and not a.no_cpu_baseline:
         it_full = ref["iters"] if ref else None
         per_it, t_setup, it, th = oracle_sample(dims, planes, seconds=15.0)
@@ -358,7 +388,28 @@ def run_ours(a, rank, world, local):
             line["cpu_baseline"] = {"value": 1.0 / per_it / 1.0, "unit": "CG iterations/s",
                                     "cores": th, "kind": "oracle",
                                     "sample": f"{it} oracle CG iterations on the full network"}
+        line["cpu_baseline"]["full_solve_64x64"] = oracle_full_small(th)
     print(json.dumps(line), flush=True)
+
+
+def oracle_full_small(threads_all):
+    """One full oracle solve of the 64 x 64 workload (g = 10^U(-1,1)) to a
+    1e-12 relative residual, wall-clock, on one thread and on all cores."""
+    import oracle
+    from paper_1908_03301_gb300 import netgen
+
+    dims, planes, _ = netgen.workload_small("random")
+    out = {"workload": "2D 64x64, g=10^U(-1,1), tol 1e-12", "cores": threads_all}
+    for key, nth in (("one_thread_s", 1), ("all_cores_s", threads_all)):
+        best = None
+        for _ in range(5):
+            t = time.perf_counter()
+            r = oracle.solve(dims, planes, tol=1e-12, nthreads=nth)
+            dt = time.perf_counter() - t
+            best = dt if best is None else min(best, dt)
+        out[key] = best
+        out["iters"] = r.iters
+    return out
 
 
 def run_profile_solve(a):
@@ -394,6 +445,10 @@ def _clocked(fn):
 
 
 def run_perc3d(a):
+    print(json.dumps(perc3d_line(a, a.steps, a.warmup, max(1, a.fp64_steps))), flush=True)
+
+
+def perc3d_line(a, n_steps, n_warmup, n_fp64):
     """256^3 bond percolation (p = 0.26, FP32 conductances from a 3D FBM):
     labelling + mixed solve per step, FP64 solve beside it."""
     import torch
@@ -425,40 +480,51 @@ def run_perc3d(a):
             res.append(r)
         return ms, res
 
-    (ms, res), clocks = _clocked(lambda: steps(ns.NET_MIXED, a.steps, a.warmup))
-    ms64, res64 = steps(ns.NET_FP64, max(1, a.fp64_steps), 1)
+    (ms, res), clocks = _clocked(lambda: steps(ns.NET_MIXED, n_steps, n_warmup))
+    ms64, res64 = steps(ns.NET_FP64, n_fp64, 1)
     r0 = res[-1]
     N = dims[0] * dims[1] * dims[2]
     b_alg = 44 * r0.n_solved  # 32 + 4d bytes per unknown of the linear system
     it_s = r0.inner_ms / 1e3 / max(1, r0.inner_iters)
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    peak = measured_hbm_peak()[0]
     # one launch per inner solve: the compacted solve; otherwise lattice sweeps
     compact = r0.inner_launches <= 2 * max(1, r0.outer_iters)
     ref = stored_oracle("perc256_x")
     line = {"metric": METRIC, "workload": "perc3d", "value": len(ms) / (sum(ms) / 1e3),
             "unit": "solves/s", "ms_per_step": statistics.mean(ms), "p50_ms": statistics.median(ms),
-            "steps": len(ms), "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "steps": len(ms), "warmup": n_warmup, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "3D 256^3 bond percolation p=0.26, FBM H=0.3 sigma=1, FP32 "
                                    "conductances", "nodes": N, "n_active": r0.n_active,
                        "n_solved": r0.n_solved, "tol_rel": TOL_REL},
             "accuracy": {"g_eff": r0.g_eff, "g_eff_fp64": res64[-1].g_eff,
                          "rel_mixed_vs_fp64": abs(r0.g_eff - res64[-1].g_eff) / max(abs(res64[-1].g_eff), 1e-300),
                          "rel_err_vs_oracle": (abs(r0.g_eff - ref["g_eff"]) / ref["g_eff"]) if ref else None,
+                         "rel_residual": r0.rel_residual, "max_imbalance": r0.max_imbalance,
                          "outer_iters": r0.outer_iters, "inner_iters": r0.inner_iters,
                          "fp64_fallback": r0.fp64_fallback},
             "fp64_cg": {"value": len(ms64) / (sum(ms64) / 1e3), "unit": "solves/s",
-                        "ms_per_step": statistics.mean(ms64), "inner_iters": res64[-1].inner_iters},
-            "inner": {"kernel": "compact_cg_kernel (listed unknowns)" if compact else "sweep_kernel (lattice)",
-                      "us_per_iteration": it_s * 1e6,
-                      "algorithmic_gbs": b_alg / it_s / 1e9, "frac": b_alg / it_s / 1e9 / peak,
-                      "bytes_note": "algorithmic = 44 B x unknowns of the linear system (after cluster "
-                                    "and dead-end stripping) per CG iteration; peak = measured copy"},
+                        "ms_per_step": statistics.mean(ms64), "inner_iters": res64[-1].inner_iters,
+                        "speedup_mixed_over_fp64": statistics.mean(ms64) / statistics.mean(ms)},
+            "roofline": {"bound": "hbm", "kernel": "compact_cg_kernel (listed unknowns)" if compact
+                         else "sweep_kernel (lattice)",
+                         "us_per_iteration": it_s * 1e6,
+                         "achieved": b_alg / it_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": b_alg / it_s / 1e9 / peak,
+                         "unknown_iterations_per_s": r0.n_solved / it_s,
+                         "bytes_note": "achieved = 44 B x unknowns of the linear system (after cluster "
+                                       "stripping and removal of dead-end trees and loops) per CG "
+                                       "iteration / inner-loop time per iteration; peak = measured copy"},
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batch(a, rank=0, world=1, local=0):
+    line = batch_line(a, rank, world, local, a.steps, a.warmup)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def batch_line(a, rank, world, local, n_steps, n_warmup):
     """512 independent 2D networks (sides 64..1024, lognormal sigma=1, even
     ones percolated at p=0.55) created and solved together per step.  Under
     torchrun the networks are shared out over the ranks (longest first by
@@ -489,13 +555,13 @@ def run_batch(a, rank=0, world=1, local=0):
         if world > 1:
             torch.distributed.barrier()
 
-    for _ in range(a.warmup):
+    for _ in range(n_warmup):
         one()
     torch.cuda.synchronize()
     barrier()
     times, res = [], None
     with Clocks(local) as clk:
-        for _ in range(a.steps):
+        for _ in range(n_steps):
             flush.zero_()
             torch.cuda.synchronize()
             barrier()
@@ -505,47 +571,62 @@ def run_batch(a, rank=0, world=1, local=0):
             times.append(replicas.max_over_ranks(time.perf_counter() - t, device=dev))
     clocks = clk.summary()
     local_res = {i: (r.status, r.inner_iters * r.n_solved, r.ms, r.fp64_fallback,
-                     r.inner_iters * specs[k][0][0] * specs[k][0][1])
+                     r.inner_iters * specs[k][0][0] * specs[k][0][1], r.g_eff_err)
                  for k, (i, r) in enumerate(zip(mine, res))}
     allr = replicas.gather_results(local_res, a.batch_count)
     if rank != 0:
-        return
+        return None
     ui = sum(x[1] for x in allr)
     li = sum(x[4] for x in allr)
     ok = sum(x[0] == 0 for x in allr)
     lat = sorted(x[2] for x in allr)
+    peak = measured_hbm_peak()[0]
+    alg = 40 * ui / statistics.mean(times) / 1e9
     line = {"metric": METRIC, "workload": "batch", "value": a.batch_count * len(times) / sum(times),
             "unit": "solves/s", "n_gpus": world, "ms_per_step": statistics.mean(times) * 1e3,
-            "steps": len(times), "warmup": a.warmup, "scaling": "strong", "dtype": "f32+f64",
+            "steps": len(times), "warmup": n_warmup, "scaling": "strong", "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": f"{a.batch_count} 2D networks, sides U{{64..1024}}, lognormal "
                                    "sigma=1, even ones percolated p=0.55; created + net_solve_batch",
                        "nodes": nodes, "tol_rel": TOL_REL,
                        "parallelism": f"networks sharded over {world} GPU(s), no collective"},
             "converged": ok, "unknown_iterations_per_s": ui / statistics.mean(times),
-            "algorithmic_gbs": 40 * ui / statistics.mean(times) / 1e9,
+            "algorithmic_gbs": alg,
             "lattice_gbs": 40 * li / statistics.mean(times) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": "sweep_kernel (all running networks per launch)",
+                         "achieved": alg, "peak": peak, "unit": "GB/s", "frac": alg / peak,
+                         "lattice_frac": 40 * li / statistics.mean(times) / 1e9 / peak,
+                         "note": "whole-batch wall time including set-up; achieved counts 40 B per "
+                                 "unknown of each linear system per CG iteration"},
+            "accuracy": {"max_g_eff_err_estimate": max(x[5] for x in allr)},
             "bytes_note": "algorithmic = 40 B x unknowns in the linear system (dead ends and "
                           "non-spanning clusters excluded) x CG iterations; lattice = 40 B x "
                           "all lattice nodes x CG iterations (what the sweep streams)",
             "per_network_ms_p50": lat[len(lat) // 2], "per_network_ms_p99": lat[int(0.99 * (len(lat) - 1))],
             "fp64_fallbacks": sum(x[3] for x in allr), "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serve(a):
+    print(json.dumps(serve_line(a, a.serve_requests, (0.25, 0.5, 0.8), max(32, a.serve_requests // 2))),
+          flush=True)
+
+
+def serve_line(a, n_sat, fracs, n_sweep):
     """Poisson request stream of mixed networks (70 % 2D sides 32..1024, 30 %
     3D sides 16..128; FBM or lognormal; 20 % near-critical percolation)
-    through the queue with a 150 GB budget.  A pool of distinct requests is
-    generated up front and cycled; the offered rate is --serve-rate, then a
-    sweep at 0.25 / 0.5 / 0.8 of the measured capacity."""
-    import threading
-
+    through the queue with a 150 GB budget.  n_sat distinct requests (fresh
+    seeded draws, generated up front) arrive at --serve-rate (saturation);
+    then, for each fraction in fracs, the first n_sweep of them at that
+    fraction of the measured capacity.  Per-request accuracy: the solver's
+    first-order estimate of the relative G_eff error, maximum over requests."""
     from paper_1908_03301_gb300 import netgen
     from paper_1908_03301_gb300 import netsolve as ns
 
     ns.lib(build_if_missing=True)
-    pool = [netgen.request_instance(i) for i in range(48)]
+    t = time.perf_counter()
+    pool = [netgen.request_instance(i) for i in range(max(n_sat, n_sweep, 16))]
+    gen_s = time.perf_counter() - t
 
     def run(rate, n):
         arr = netgen.poisson_arrivals(n, rate)
@@ -556,7 +637,7 @@ def run_serve(a):
                 dt = arr[i] - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
-                d, pl = pool[i % len(pool)]
+                d, pl = pool[i]
                 tickets.append(q.submit(d, pl))
             results = [q.wait(t, timeout_ms=600000) for t in tickets]
             t1 = time.perf_counter()
@@ -567,21 +648,28 @@ def run_serve(a):
             name = ns.STATUS_NAMES[st] if 0 <= st < len(ns.STATUS_NAMES) else str(st)
             counts[name] = counts.get(name, 0) + 1
         errors = sorted({r.error for st, r in results if st != 0 and r is not None})[:4]
+        worst = max((r.g_eff_err for st, r in results if st == 0 and r is not None), default=None)
         return {"offered_rate": rate, "requests": n, "ok": ok, "status_counts": counts, "errors": errors,
-                "solves_per_s": n / (t1 - t0), "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0}
+                "solves_per_s": n / (t1 - t0), "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0,
+                "max_g_eff_err_estimate": worst}
 
     run(50.0, 16)  # warm-up
-    sat = run(a.serve_rate, a.serve_requests)
+    with Clocks(0) as clk:
+        sat = run(a.serve_rate, n_sat)
+    clocks = clk.summary()
     cap = sat["solves_per_s"]
-    sweep = [run(f * cap, max(32, a.serve_requests // 2)) for f in (0.25, 0.5, 0.8)]
+    sweep = [run(f * cap, n_sweep) for f in fracs]
     line = {"metric": METRIC, "workload": "serve", "value": sat["solves_per_s"], "unit": "solves/s",
             "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"], "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "Poisson stream, 70% 2D (32..1024) / 30% 3D (16..128), FBM or "
-                                   "lognormal, 20% near-critical percolation, 150 GB budget; a pool "
-                                   "of 48 distinct requests cycled",
-                       "tol_rel": TOL_REL},
-            "saturated": sat, "sweep": sweep}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": f"Poisson stream at {a.serve_rate:g}/s, 70% 2D (32..1024) / 30% 3D "
+                                   f"(16..128), FBM or lognormal, 20% near-critical percolation, 150 GB "
+                                   f"budget; {n_sat} distinct requests (seeded draws)",
+                       "tol_rel": TOL_REL, "generation_s": gen_s},
+            "latency_note": "p50/p99 from arrival to result; at saturation they are dominated by "
+                            "queueing (the offered rate is above capacity), the sweep gives service "
+                            "latency below capacity",
+            "saturated": sat, "sweep": sweep, "clocks": clocks}
+    return line
 
 
 def run_aniso(a):
@@ -667,8 +755,7 @@ def run_periodic(a):
     r0 = res[-1]
     b_alg = 40 * r0.n_solved  # 32 + 4d bytes per unknown and iteration, d = 2
     it_s = r0.inner_ms / 1e3 / max(1, r0.inner_iters)
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    peak = measured_hbm_peak()[0]
     line = {"metric": METRIC, "workload": "periodic", "value": len(ms) / (sum(ms) / 1e3),
             "unit": "solves/s", "ms_per_step": statistics.mean(ms), "steps": len(ms),
             "warmup": a.warmup, "dtype": "f32+f64", "data": "synthetic",

@@ -165,6 +165,10 @@ typedef struct {
     double g_eff_err;        /* estimated relative error of g_eff (see tol_geff) */
     int64_t n_solved;        /* unknowns of the linear system: n_active less the
                                 dead-end nodes (see net_get_backbone) */
+    double queue_ms;         /* netq_* only: time from netq_submit to admission
+                                onto the device (0 for net_solve / batches) */
+    int64_t co_running;      /* netq_* only: requests already running on the
+                                device when this one was admitted */
 } net_result;
 
 /* Fill *opts with the defaults listed in net_opts. */

@@ -35,10 +35,9 @@ namespace {
 
 constexpr int CT = 512;                 // threads per CTA
 constexpr int CW = CT / 32;
-constexpr int UNR = 2;                  // unknowns a thread keeps in flight (FP64)
+constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP64; more spill)
 constexpr int UNR32 = 2;                // the same in FP32
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
-constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
@@ -179,9 +178,11 @@ __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------ refinement glue
+// The armed residual is r_{iter-1}: it goes into set (iter + 1) & 1.
 template <typename T>
 __global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx, const T *__restrict__ src,
-                                      T *dst) {
+                                      T *r0, T *r1, const InnerScal *is) {
+    T *dst = (is->iter & 1) ? r0 : r1;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
          k += (long long)gridDim.x * blockDim.x)
         dst[k] = src[cidx[k]];
@@ -191,9 +192,11 @@ __global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx,
 // alpha_k p_k (the recursion continues): fold it in and clear y.
 template <typename T>
 __global__ void compact_correct_kernel(long long U, const int *__restrict__ cidx, const double *__restrict__ dis,
-                                       double *x, T *y, const T *__restrict__ p, const InnerScal *is) {
+                                       double *x, T *y, const T *p0, const T *p1, const InnerScal *is) {
     const bool owe = is->stop == 6;
     const double a = is->alpha;
+    // the last iteration k = iter - 1 wrote p_k into set k & 1
+    const T *__restrict__ p = (is->iter & 1) ? p0 : p1;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
          k += (long long)gridDim.x * blockDim.x) {
         double d = (double)y[k];
@@ -209,30 +212,39 @@ __global__ void compact_correct_kernel(long long U, const int *__restrict__ cidx
 // ------------------------------------------------------------------ the solve
 // Grid barrier part 1: every CTA's writes are done; thread 0 arrives.
 // Returns (to all threads) whether this CTA arrived last at barrier `target`.
-__device__ __forceinline__ bool barrier_arrive(unsigned *count, unsigned target, int G) {
+// `withhold`: for tests of the bounded wait, this CTA does not arrive.
+__device__ __forceinline__ bool barrier_arrive(unsigned *count, unsigned target, int G, bool withhold) {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u) + 1u;
-        s_last = arrived == (unsigned)G * target;
+        if (withhold) {
+            s_last = 0;
+        } else {
+            const unsigned arrived = atomicAdd(count, 1u) + 1u;
+            s_last = arrived == (unsigned)G * target;
+        }
     }
     __syncthreads();
     return s_last != 0;
 }
 // Grid barrier part 2 for the CTAs that did not arrive last (thread 0 waits
-// for the release); returns false if the wait gave up.
-__device__ __forceinline__ bool barrier_wait(const unsigned *gen, unsigned target) {
+// for the release); returns false if the wait gave up (after wait_ns of
+// device time).
+__device__ __forceinline__ bool barrier_wait(const unsigned *gen, unsigned target, unsigned long long wait_ns) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         // poll with relaxed loads (an acquire per poll would order, and slow,
         // the memory traffic of the other CTA on this SM), then one acquire
         bool ok = false;
-        for (uint32_t i = 0; i < SPIN_LIMIT; i++)
+        const unsigned long long t0 = globaltimer_ns();
+        for (uint32_t i = 0;; i++) {
             if (ld_relaxed_u32(gen) >= target) {
                 ok = ld_acquire_u32(gen) >= target;
                 break;
             }
+            if ((i & 255u) == 255u && globaltimer_ns() - t0 > wait_ns) break;
+        }
         s_ok = ok;
     }
     __syncthreads();
@@ -243,16 +255,37 @@ __device__ __forceinline__ void barrier_release(unsigned *gen, unsigned target) 
     st_release_u32(gen, target);
 }
 
+// Iteration k (st.iter) reads r_{k-1}, p_{k-1}, q_{k-1} from set (k+1)&1 and
+// writes r_k, p_k, q_k into set k&1 (the armed residual is r_{-1}, in set 1
+// at a fresh start).  CTA c owns the contiguous list range [u0, u1); its p_k
+// is also kept in shared memory (when the range fits) for the operator.
+// A neighbour outside the range is another CTA's: its p_k is formed here from
+// that CTA's r_{k-1}, q_{k-1}, p_{k-1}, which nobody writes during
+// iteration k -- so one grid barrier per iteration suffices.
+template <typename T>
+struct PrevSet {
+    const T *r, *p, *q;
+    T alpha, beta;
+    bool first;
+    __device__ __forceinline__ T p_of(int j) const {
+        const T rj = __ldcg(r + j);
+        if (first) return rj;
+        return fma(beta, __ldcg(p + j), fma(-alpha, __ldcg(q + j), rj));
+    }
+};
+
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    T *sp = reinterpret_cast<T *>(dyn);  // p_k of this CTA's range (when it fits)
     __shared__ InnerScal st;
     __shared__ T s_red[CW][4];
     const int G = gridDim.x, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *__restrict__ y = (T *)a.y;
-    T *__restrict__ r = (T *)a.r;
-    T *p = (T *)a.p;
-    T *__restrict__ q = (T *)a.q;
+    T *rs[2] = {(T *)a.r, (T *)a.r2};
+    T *ps[2] = {(T *)a.p, (T *)a.p2};
+    T *qs[2] = {(T *)a.q, (T *)a.q2};
     const T *__restrict__ val = (const T *)a.val;
     const int *__restrict__ nbr = a.nbr;
     unsigned *bar_count = a.bar, *bar_gen = a.bar + 1;
@@ -263,89 +296,96 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
     }
     __syncthreads();
     // list indices fit in 32 bits (the table stores them as int)
-    const int tid = c * CT + (int)threadIdx.x, nth = G * CT;
     const int U = (int)a.n;
+    const int u0 = (int)((long long)U * c / G), u1 = (int)((long long)U * (c + 1) / G);
+    const bool staged = u1 - u0 <= a.stage_cap;
     constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    constexpr int STEP = UN * CT;
+    const long long VS = U + 1;  // val slot stride
     unsigned target = 0;
-    bool bad = false;
     while (st.stop == 0) {
         const bool first = st.iter == 0;
         const T alpha = (T)st.alpha, beta = (T)st.beta;
-        // ---- phase A: finish iteration k-1 (UN unknowns in flight per thread) ----
-        for (int k0 = tid; k0 < U; k0 += UN * nth) {
+        const int cur = (int)(st.iter & 1), prv = cur ^ 1;
+        T *__restrict__ rn = rs[cur];
+        T *__restrict__ pn = ps[cur];
+        T *__restrict__ qn = qs[cur];
+        const PrevSet<T> old{rs[prv], ps[prv], qs[prv], alpha, beta, first};
+        // ---- phase A: finish iteration k-1 on the own range ----
+        for (int k0 = u0 + (int)threadIdx.x; k0 < u1; k0 += STEP) {
             T rk[UN], pk[UN], qk[UN], yk[UN];
 #pragma unroll
             for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * nth;
-                if (k < U) {
-                    rk[u] = r[k];
+                const int k = k0 + u * CT;
+                if (k < u1) {
+                    rk[u] = old.r[k];
                     if (!first) {
-                        pk[u] = p[k];
-                        qk[u] = q[k];
+                        pk[u] = old.p[k];
+                        qk[u] = old.q[k];
                         yk[u] = y[k];
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * nth;
-                if (k >= U) continue;
+                const int k = k0 + u * CT;
+                if (k >= u1) continue;
+                T r1 = rk[u], p1 = rk[u];
                 if (first) {
-                    p[k] = rk[u];
                     y[k] = T(0);
                 } else {
-                    const T rn = fma(-alpha, qk[u], rk[u]);
-                    r[k] = rn;
+                    r1 = fma(-alpha, qk[u], rk[u]);
+                    p1 = fma(beta, pk[u], r1);
                     y[k] = fma(alpha, pk[u], yk[u]);
-                    p[k] = fma(beta, pk[u], rn);
                 }
+                rn[k] = r1;
+                pn[k] = p1;
+                if (staged) sp[k - u0] = p1;
             }
         }
-        ++target;
-        if (barrier_arrive(bar_count, target, G)) {
-            if (threadIdx.x == 0) barrier_release(bar_gen, target);
-        } else if (!barrier_wait(bar_gen, target)) {
-            bad = true;
-        }
         __syncthreads();
-        // ---- phase B: q = A p and the four sums ----
+        // ---- phase B: q_k = A p_k and the four sums on the own range ----
         T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
-        const long long VS = U + 1;  // val slot stride
-        for (int k0 = tid; k0 < U; k0 += UN * nth) {
+        auto pget = [&](int j) -> T {
+            if (j >= u0 && j < u1) return staged ? sp[j - u0] : __ldcg(pn + j);
+            return old.p_of(j);
+        };
+        for (int k0 = u0 + (int)threadIdx.x; k0 < u1; k0 += STEP) {
             T wxp[UN], wxm[UN], wp[UN][NDIM - 1];
             int ip[UN][NDIM - 1], im[UN][NDIM - 1];
 #pragma unroll
             for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * nth;
-                const bool ok = k < U;
-                const int kk = ok ? k : 0;
+                const int k = k0 + u * CT;
+                const bool ok = k < u1;
+                const int kk = ok ? k : u0;
                 wxp[u] = ok ? __ldg(val + kk) : T(0);
                 wxm[u] = (ok && k > 0) ? __ldg(val + kk - 1) : T(0);
 #pragma unroll
                 for (int d = 1; d < NDIM; d++) {
                     wp[u][d - 1] = ok ? __ldg(val + d * VS + kk) : T(0);
-                    ip[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1)) * U + kk) : (int)kk;
-                    im[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + kk) : ~(int)kk;
+                    ip[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1)) * U + kk) : kk;
+                    im[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + kk) : ~kk;
                 }
             }
 #pragma unroll
             for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * nth;
-                if (k >= U) continue;
-                const T pk = __ldcg(p + k);
-                T nb = wxp[u] * __ldcg(p + k + 1);
-                nb = fma(wxm[u], __ldcg(p + (k > 0 ? k - 1 : 0)), nb);
+                const int k = k0 + u * CT;
+                if (k >= u1) continue;
+                const T pk = staged ? sp[k - u0] : __ldcg(pn + k);
+                T nb = wxp[u] != T(0) ? wxp[u] * pget(k + 1) : T(0);
+                if (wxm[u] != T(0)) nb = fma(wxm[u], pget(k - 1), nb);
 #pragma unroll
                 for (int d = 1; d < NDIM; d++) {
-                    nb = fma(wp[u][d - 1], __ldcg(p + ip[u][d - 1]), nb);
+                    if (wp[u][d - 1] != T(0)) nb = fma(wp[u][d - 1], pget(ip[u][d - 1]), nb);
                     const int jm = im[u][d - 1];
-                    const int jj = jm >= 0 ? jm : ~jm;
-                    const T wm = jm >= 0 ? __ldg(val + d * VS + jj) : T(0);
-                    nb = fma(wm, __ldcg(p + jj), nb);
+                    if (jm >= 0) {
+                        const T wm = __ldg(val + d * VS + jm);
+                        if (wm != T(0)) nb = fma(wm, pget(jm), nb);
+                    }
                 }
                 const T qk = pk - nb;
-                q[k] = qk;
-                const T rk = r[k];
+                qn[k] = qk;
+                const T rk = __ldcg(rn + k);
                 s_pq = fma(pk, qk, s_pq);
                 s_rq = fma(rk, qk, s_rq);
                 s_qq = fma(qk, qk, s_qq);
@@ -361,19 +401,18 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
 #pragma unroll
             for (int k = 0; k < 4; k++) s_red[warp][k] = t4[k];
         __syncthreads();
-        const int par = (int)(st.iter & 1);
+        const int par = cur;
         if (threadIdx.x == 0) {
             double tot[4] = {0, 0, 0, 0};
             for (int w = 0; w < CW; w++)
 #pragma unroll
                 for (int k = 0; k < 4; k++) tot[k] += (double)s_red[w][k];
-            if (bad) tot[0] = tot[1] = tot[2] = tot[3] = NAN;
 #pragma unroll
             for (int k = 0; k < 4; k++) a.pb[((long long)par * G + c) * 4 + k] = tot[k];
         }
         ++target;
         bool ok = true;
-        if (barrier_arrive(bar_count, target, G)) {
+        if (barrier_arrive(bar_count, target, G, target == 1u && c == a.skip_cta)) {
             // the last CTA: one warp sums the partials (lanes stride over
             // the CTAs, fixed order, FP64), advances the state, releases
             if (warp == 0) {
@@ -397,7 +436,7 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 }
             }
         } else {
-            ok = barrier_wait(bar_gen, target);
+            ok = barrier_wait(bar_gen, target, a.wait_ns);
             if (threadIdx.x == 0) {
                 if (!ok) {
                     st.stop = 5;
@@ -408,7 +447,7 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 }
             }
         }
-        if (threadIdx.x == 0 && (bad || !ok)) {
+        if (threadIdx.x == 0 && !ok) {
             atomicExch(a.err, 1);
             st.stop = 5;
         }
@@ -422,13 +461,21 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
     }
 }
 
+// Shared memory for the staged p of a CTA's range (two CTAs per SM).
+constexpr int STAGE_BYTES = 64 * 1024;
+
 template <typename T, int NDIM>
 cudaError_t launch_cg_t(const CompactArgs &a, int grid, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     CompactArgs arg = a;
+    const long long range = (a.n + grid - 1) / grid;  // the largest CTA range
+    const long long cap = STAGE_BYTES / (long long)sizeof(T);
+    arg.stage_cap = range <= cap ? (int)range : 0;
+    const size_t smem = (size_t)arg.stage_cap * sizeof(T);
     void *params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CT), params, 0,
+    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CT), params, smem,
                                        st);
 }
 
@@ -437,7 +484,8 @@ int grid_t() {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compact_cg_kernel<T, NDIM>, CT, 0);
+    cudaFuncSetAttribute(compact_cg_kernel<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compact_cg_kernel<T, NDIM>, CT, STAGE_BYTES);
     if (nsm < 1) nsm = 1;
     if (per < 1) per = 1;
     return nsm * per;
@@ -494,22 +542,25 @@ cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f3
     return e;
 }
 
-cudaError_t launch_compact_gather(long long U, const int *cidx, const void *src, void *dst, int f32,
-                                  cudaStream_t st) {
+cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st) {
+    const long long U = a.n;
     if (f32)
-        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, cidx, (const float *)src, (float *)dst);
+        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const float *)src, (float *)a.r,
+                                                                (float *)a.r2, a.s);
     else
-        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, cidx, (const double *)src, (double *)dst);
+        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const double *)src, (double *)a.r,
+                                                                 (double *)a.r2, a.s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_correct(long long U, const int *cidx, const double *dis, double *x, void *y,
-                                   const void *p, const InnerScal *is, int f32, cudaStream_t st) {
+cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, double *x, int f32, cudaStream_t st) {
+    const long long U = a.n;
     if (f32)
-        compact_correct_kernel<float><<<nb_for(U), 256, 0, st>>>(U, cidx, dis, x, (float *)y, (const float *)p, is);
+        compact_correct_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, dis, x, (float *)a.y, (const float *)a.p,
+                                                                 (const float *)a.p2, a.s);
     else
-        compact_correct_kernel<double><<<nb_for(U), 256, 0, st>>>(U, cidx, dis, x, (double *)y, (const double *)p,
-                                                                   is);
+        compact_correct_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, dis, x, (double *)a.y,
+                                                                  (const double *)a.p, (const double *)a.p2, a.s);
     return cudaGetLastError();
 }
 

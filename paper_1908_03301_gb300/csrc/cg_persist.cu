@@ -42,7 +42,6 @@ constexpr int BAR = 128;
 constexpr int HALO = S * NARR * ROWB;  // offset of the halo rows (after BAR)
 constexpr int SMEM = BAR + HALO + 6 * ROWB;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
-constexpr uint32_t SPIN_LIMIT = 1u << 24;
 static_assert(SMEM <= 227 * 1024, "shared memory");
 
 enum { A_R = 0, A_Q = 1, A_P = 2, A_Y = 3, A_GX = 4, A_GY = 5 };
@@ -397,10 +396,15 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             asm volatile("fence.proxy.async.global;" ::: "memory");
             for (; pre < S && pre < steps; pre++) producer_issue(pre - 1, false);
         } else if (threadIdx.x == 0) {
-            // grid barrier, part 1: arrive
+            // grid barrier, part 1: arrive (a CTA told to withhold its
+            // first arrival, for tests of the bounded wait, does not)
             __threadfence();
-            const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
-            s_last = arrived == (unsigned)G * target;
+            if (sweep == 0 && c == a.skip_cta) {
+                s_last = 0;
+            } else {
+                const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
+                s_last = arrived == (unsigned)G * target;
+            }
             if (s_bad) atomicExch(a.err, 1);
         }
         __syncthreads();  // B
@@ -433,12 +437,15 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             // grid barrier, part 2: wait for the release, read the new state
             // relaxed polls, then one acquire: an acquire per poll would
             // order (and slow) this SM's other memory traffic
+            // (gives up after a.wait_ns of device time)
             bool ok = false;
-            for (uint32_t i = 0; i < SPIN_LIMIT; i++) {
+            const unsigned long long t0 = globaltimer_ns();
+            for (uint32_t i = 0;; i++) {
                 if (ld_relaxed(a.bar_gen) >= target) {
                     ok = ld_acquire(a.bar_gen) >= target;
                     break;
                 }
+                if ((i & 255u) == 255u && globaltimer_ns() - t0 > a.wait_ns) break;
             }
             if (!ok) {
                 atomicExch(a.err, 1);
@@ -523,6 +530,7 @@ cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     e = cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned) * 2, st);  // arrivals and generation
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     PersistArgs arg = a;
     void *params[] = {&arg};

@@ -230,6 +230,13 @@ __device__ __forceinline__ void finish_iteration(InnerScal *s, long long k, cons
     else if (k - s->best_iter > s->stag_window) s->stop = 3;
 }
 
+// Device clock in nanoseconds (bounds the grid-barrier waits in time).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // 16-byte vector of T (float4 / double2) with element access.
 template <typename T> struct Vec;
 template <> struct Vec<float> {

@@ -24,6 +24,16 @@ cudaError_t launch_prune_round(const Geom &g, const void *const graw[3], int f32
                                cudaStream_t st);
 cudaError_t launch_prune_finish(const Geom &g, uint8_t *cls, const unsigned int *pr, int *root,
                                 int passes, cudaStream_t st);
+// Dead-end loops (blocks.cu): the spanning nodes still CLS_SPANNING that lie
+// outside the biconnected component of the extra inlet-outlet edge become
+// CLS_DANGLING with root = the node their part hangs from; roots of earlier
+// dead-end nodes are re-resolved.  root: L ints, -1 where not removed;
+// vmap: L ints of scratch.  *removed: nodes marked; *internal_err != 0 if a
+// consistency check failed (nothing was marked).  Allocates its other
+// scratch (about 4 (2d + 25) bytes per spanning node) on the stream and
+// returns after the work has finished.
+cudaError_t strip_dead_loops(const Geom &g, const void *const graw[3], int f32, uint8_t *cls, int *root,
+                             int *vmap, long long *removed, int *internal_err, cudaStream_t st);
 // x at every dead-end node := x at its root (root[i] = -1 elsewhere).
 cudaError_t launch_fill_dangling(const Geom &g, const int *root, double *x, cudaStream_t st);
 // Compact uint8 mask of the backbone (spanning nodes left in the system).
@@ -65,7 +75,9 @@ struct PersistArgs {
     InnerScal *bc;             // state published by the barrier [2]
     unsigned *bar_count;       // grid barrier: arrivals (bar_count[0]) and
     unsigned *bar_gen;         //   generation (bar_gen == bar_count + 1)
-    int *err;
+    int *err;                  // set when a bounded wait gave up (cleared at launch)
+    unsigned long long wait_ns;  // give up a grid-barrier wait after this long
+    int skip_cta;              // testing: this CTA withholds its first arrival (-1: none)
 };
 bool persist_applies(const Geom &g, int f32);
 int persist_grid(const Geom &g);
@@ -75,7 +87,10 @@ cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st);
 // ---- inner solve over a compacted list of unknowns (cg_compact.cu) --------
 struct CompactArgs {
     long long n;            // unknowns
-    void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each
+    void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each; r, p, q
+    void *r2, *p2, *q2;     //   are double-buffered (set 0, set 1)
+    const int *cidx;        // lattice index of each unknown
+    int stage_cap;          // set at launch: p entries staged in shared memory
     const void *val;        // scaled +e_d bonds [ndim][n + 1] (T; 0: none)
     const int *nbr;         // list indices of the +-e_d neighbours, d = y[, z]:
                             // [2 (ndim - 1)][n]; none: k (+e_d), ~k (-e_d)
@@ -83,19 +98,20 @@ struct CompactArgs {
     InnerScal *bc;          // state published by the grid barrier [2]
     double *pb;             // per-CTA partial sums [2][grid][4]
     unsigned *bar;          // grid barrier: arrivals, generation
-    int *err;               // set when a bounded wait gave up
+    int *err;               // set when a bounded wait gave up (cleared at launch)
+    unsigned long long wait_ns;  // give up a grid-barrier wait after this long
+    int skip_cta;           // testing: this CTA withholds its first arrival (-1: none)
 };
 int compact_grid(int ndim, int f32);
 // List the unknowns (cls == CLS_SPANNING) in lattice order and build their
 // ELL rows from the scaled lattice bonds gs (T).  cmap: L-entry scratch.
 cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f32, const void *const gs[3],
                           int *cmap, int *cidx, int *nbr, void *val, cudaStream_t st);
-// dst[k] = src[cidx[k]] (lattice -> list, T)
-cudaError_t launch_compact_gather(long long U, const int *cidx, const void *src, void *dst, int f32,
-                                  cudaStream_t st);
+// r[k] = src[cidx[k]] (lattice -> list, T), into the r set the armed inner
+// solve reads first (set (iter + 1) & 1)
+cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st);
 // x[cidx[k]] += D^-1/2 (y[k] (+ alpha p[k] when the pass ended with stop 6))
-cudaError_t launch_compact_correct(long long U, const int *cidx, const double *dis, double *x, void *y,
-                                   const void *p, const InnerScal *is, int f32, cudaStream_t st);
+cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, double *x, int f32, cudaStream_t st);
 cudaError_t launch_compact_cg(const CompactArgs &a, int ndim, int f32, int grid, cudaStream_t st);
 
 // ---- persistent sweep over segmented networks (sweep.cu) -------------------

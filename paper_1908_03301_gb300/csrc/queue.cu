@@ -41,7 +41,8 @@ struct Req {
     std::string err;  // error message of a request that ended non-OK
     BatchItem item;
     net_t *net = nullptr;
-    std::chrono::steady_clock::time_point t_submit;
+    std::chrono::steady_clock::time_point t_submit, t_admit;
+    long long co_running = 0;  // requests on the device when this one was admitted
 };
 
 }  // namespace
@@ -67,6 +68,10 @@ namespace {
 
 void finalize_locked(netq_t *q, Req *r, net_status st) {
     r->res.status = st;
+    if (r->state == Q_RUNNING) {
+        r->res.queue_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+        r->res.co_running = r->co_running;
+    }
     if (st != NET_OK && r->err.empty()) r->err = last_error();
     r->state = Q_DONE;
     q->lat_ms.push_back(
@@ -88,6 +93,8 @@ void worker_main(netq_t *q) {
                 Req *r = q->pending.front();
                 q->pending.pop_front();
                 r->state = Q_RUNNING;
+                r->t_admit = std::chrono::steady_clock::now();
+                r->co_running = (long long)eng.running();
                 q->used += r->foot;
                 q->running++;
                 admit.push_back(r);

@@ -140,6 +140,7 @@ size_t net_footprint_bytes(const Geom &g, int raw_f32) {
     b += 7 * L * 4;                          // FP32 inner vectors
     b += L * 4;                              // label flags (set-up only)
     b += L * 4;                              // dead-end roots (percolated networks)
+    b += L * 4 * (2 * nd + 25);              // set-up only: dead-end loop pass (spanning nodes <= L)
     return b;
 }
 
@@ -233,7 +234,7 @@ net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
     CK(dalloc(&cd.cidx, sizeof(int) * (size_t)U, st));
     CK(dalloc(&cd.nbr, sizeof(int) * 2 * (nd - 1) * (size_t)U, st));
     CK(dalloc(&cd.val, es * nd * (size_t)(U + 1), st));
-    CK(dalloc(&cd.vec, es * 4 * (size_t)(U + 1), st));
+    CK(dalloc(&cd.vec, es * 7 * (size_t)(U + 1), st));  // y and two sets of r, p, q
     cd.grid = compact_grid(G.ndim, f32);
     CK(dalloc(&cd.bc, sizeof(InnerScal) * 2, st));
     CK(dalloc(&cd.pb, sizeof(double) * 2 * 4 * (size_t)cd.grid, st));
@@ -247,6 +248,27 @@ net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
     return NET_OK;
 }
 
+// Limit of a grid-barrier wait in the cooperative kernels: NETSOLVE_WAIT_NS
+// (device nanoseconds), default 2 s.  A wait that gives up ends the solve
+// with NET_ETIMEOUT.
+unsigned long long grid_wait_ns() {
+    const char *e = getenv("NETSOLVE_WAIT_NS");
+    if (e && *e) {
+        const long long v = atoll(e);
+        if (v > 0) return (unsigned long long)v;
+    }
+    return 2000000000ULL;
+}
+
+// Testing aid: NETSOLVE_WITHHOLD_ARRIVAL=c makes CTA c of the cooperative
+// kernels skip its first grid-barrier arrival, so that every other CTA's
+// bounded wait runs out (the way a failure detection test makes it happen
+// without faulting the GPU).  Unset: -1, no CTA withholds.
+int withheld_arrival_cta() {
+    const char *e = getenv("NETSOLVE_WITHHOLD_ARRIVAL");
+    return (e && *e) ? atoi(e) : -1;
+}
+
 CompactArgs compact_args(net_t *n, int f32) {
     const int k = f32 ? 0 : 1;
     CompactDev &cd = n->cp[k];
@@ -258,6 +280,10 @@ CompactArgs compact_args(net_t *n, int f32) {
     a.r = v + 1 * V * es;
     a.p = v + 2 * V * es;
     a.q = v + 3 * V * es;
+    a.r2 = v + 4 * V * es;
+    a.p2 = v + 5 * V * es;
+    a.q2 = v + 6 * V * es;
+    a.cidx = cd.cidx;
     a.val = cd.val;
     a.nbr = cd.nbr;
     a.s = &n->dsc->in[k];
@@ -265,6 +291,8 @@ CompactArgs compact_args(net_t *n, int f32) {
     a.pb = cd.pb;
     a.bar = cd.bar;
     a.err = cd.err;
+    a.wait_ns = grid_wait_ns();
+    a.skip_cta = withheld_arrival_cta();
     return a;
 }
 
@@ -534,10 +562,16 @@ net_status autotune_nets(const std::vector<net_t *> &nets, int f32, int default_
 // precision's type, so a switch of precision first re-arms with no correction
 // pending (see solve_impl).
 
-bool prune_enabled() {
+// NETSOLVE_PRUNE: "0" keeps every spanning node in the linear system,
+// "trees" strips dead-end trees only, anything else (the default) strips
+// dead-end trees and then dead-end loops (the current-carrying backbone).
+int prune_level() {
     const char *e = getenv("NETSOLVE_PRUNE");
-    return !(e && strcmp(e, "0") == 0);
+    if (e && strcmp(e, "0") == 0) return 0;
+    if (e && strcmp(e, "trees") == 0) return 1;
+    return 2;
 }
+bool prune_enabled() { return prune_level() > 0; }
 
 // Strip the dead-end trees of the spanning clusters (rounds of removing
 // nodes with at most one link left; see prune_round_kernel), then resolve
@@ -563,15 +597,26 @@ net_status prune_dead_ends(net_t *n, const void *const gr[3], unsigned int *pr) 
         total += n->hsc->ss.pruned;
         if (n->hsc->ss.pruned == 0) break;
     }
-    if (total == 0) {
+    if (total > 0) {
+        int passes = 1;
+        while ((1u << passes) <= round) passes++;
+        CK(launch_prune_finish(G, n->cls, pr, n->proot, passes + 1, st));
+        n->prune_rounds = (int)round;
+    }
+    long long loops = 0;
+    if (prune_level() >= 2) {
+        int bad = 0;
+        CK(strip_dead_loops(G, gr, n->raw_f32, n->cls, n->proot, (int *)pr, &loops, &bad, st));
+        if (bad) {
+            set_error("dead-end loop stripping: internal consistency check %d failed", bad);
+            return NET_ECUDA;
+        }
+        n->loop_nodes = loops;
+    }
+    if (total == 0 && loops == 0) {
         dfree(n->proot, st);
         n->proot = nullptr;
-        return NET_OK;
     }
-    int passes = 1;
-    while ((1u << passes) <= round) passes++;
-    CK(launch_prune_finish(G, n->cls, pr, n->proot, passes + 1, st));
-    n->prune_rounds = (int)round;
     return NET_OK;
 }
 
@@ -738,12 +783,12 @@ net_status outer_pass_single(net_t *n, int f32, int apply_corr, const net_opts &
         const CompactDev &cd = n->cp[f32 ? 0 : 1];
         const CompactArgs ca = compact_args(n, f32);
         if (apply_corr)
-            CK(launch_compact_correct(ca.n, cd.cidx, n->dis, n->x, ca.y, ca.p, ca.s, f32, st));
+            CK(launch_compact_correct(ca, n->dis, n->x, f32, st));
         OuterArgs oa = outer_args(n, f32, 0, f32, o, 1);
         oa.allow_cont = o.refine != NET_REFINE_RESTART && apply_corr;  // correction applied above
         CK(launch_outer(oa, st));
         const InnerArgs ia = inner_args(n, f32);
-        CK(launch_compact_gather(ca.n, cd.cidx, ia.r[0], ca.r, f32, st));
+        CK(launch_compact_gather(ca, ia.r[0], f32, st));
         return NET_OK;
     }
     OuterArgs oa = outer_args(n, f32, apply_corr, f32, o, use_persist_kernel(n, f32));
@@ -855,6 +900,8 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             pa.bar_count = n->ps_bar;
             pa.bar_gen = n->ps_bar + 1;
             pa.err = n->ps_err;
+            pa.wait_ns = grid_wait_ns();
+            pa.skip_cta = withheld_arrival_cta();
             CK(launch_persist_resume(pa, n->ps_grid, st));
             CK(launch_persist(pa, n->ps_grid, st));
             chunks = 0;

@@ -60,6 +60,7 @@ struct net_s {
     int *proot = nullptr;                          // dead-end node -> its root (-1 elsewhere);
                                                    // NULL when nothing was stripped
     int prune_rounds = 0;
+    long long loop_nodes = 0;  // nodes removed as parts of dead-end loops
     uint8_t *cls = nullptr;                        // cluster classes
     double *dis = nullptr;                         // D^-1/2 on solved nodes, else 0
     double *x = nullptr;                           // FP64 pressures

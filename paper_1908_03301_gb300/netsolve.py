@@ -44,7 +44,7 @@ class net_result(C.Structure):
                 ("n_active", C.c_int64), ("outer_iters", C.c_int), ("inner_iters", C.c_int64),
                 ("fp64_fallback", C.c_int), ("ms", C.c_float), ("inner_ms", C.c_float),
                 ("inner_launches", C.c_int64), ("status", C.c_int), ("g_eff_err", C.c_double),
-                ("n_solved", C.c_int64)]
+                ("n_solved", C.c_int64), ("queue_ms", C.c_double), ("co_running", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -257,6 +257,8 @@ class Result:
     status: int
     g_eff_err: float
     n_solved: int
+    queue_ms: float = 0.0  # queue: submit -> admission onto the device
+    co_running: int = 0    # queue: requests running when this one was admitted
     error: str = ""  # message of a non-OK status
 
     @classmethod
@@ -409,6 +411,11 @@ def fbm_bonds(dims, field, sigma, dtype=None, periodic=(), flow_axis=0):
     desc = make_desc(dims, flow_axis, 1.0, 0.0, bdt, 1, stream, periodic)
     _check(lib().net_fbm_bonds(C.byref(desc), field.data_ptr(), float(sigma), ptrs), "net_fbm_bonds")
     return planes
+
+
+def last_error() -> str:
+    """Message of the last failing call on this thread (net_last_error)."""
+    return lib().net_last_error().decode(errors="replace")
 
 
 def solve_batch(networks, opts: net_opts | None = None, check=True):

@@ -5,7 +5,10 @@ Calls only the oracle and the seeded input generators.  Each entry records the
 effective conductance (Eq. 4 flow / pressure drop), the CG iteration count of
 the oracle's Jacobi-PCG, its final relative residual and the wall time, so
 that the full-size parity tests and the CPU-baseline scaling can use them
-without re-running a solve of many minutes.
+without re-running a solve of many minutes.  For the 2048^2 networks it also
+stores the pressures of a strided sample of nodes (every 32nd row from row 7,
+every 32nd column from column 3: 64 x 64 nodes) for an element-by-element
+comparison.
 
     python tests/golden/make_oracle_reference.py [case ...]
 """
@@ -42,6 +45,11 @@ def main(names):
                       "max_imbalance": r.max_imbalance, "n_active": r.n_active,
                       "status": r.status, "seconds": dt, "threads": oracle.max_threads(),
                       "tol": 1e-13}
+        if len(dims) == 2:
+            rows = list(range(7, dims[1], 32))
+            cols = list(range(3, dims[0], 32))
+            data[name]["P_sample"] = {"rows": rows, "cols": cols,
+                                      "values": [[float(v) for v in r.P[y, cols]] for y in rows]}
         json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
         print(name, data[name], flush=True)
 

@@ -1,7 +1,12 @@
 """Dead-end stripping on the GPU: the backbone mask is bit-exact against the
 oracle's, the linear system shrinks to it (n_solved), and G_eff and every
 node's pressure (the stripped ones included) still match the FP64 oracle,
-which solves the whole spanning cluster."""
+which solves the whole spanning cluster.
+
+Two levels: the default removes dead-end trees and then dead-end loops (the
+current-carrying backbone: the block of the extra inlet-outlet edge, checked
+against oracle.backbone_blocks); NETSOLVE_PRUNE=trees removes the trees only
+(checked against oracle.backbone)."""
 import numpy as np
 import pytest
 
@@ -27,18 +32,29 @@ def rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
 
 
-CASES = [((40, 33), 0, 0.6, 1), ((29, 41), 1, 0.58, 2), ((23, 19, 17), 0, 0.36, 3),
-         ((18, 21, 20), 2, 0.34, 4), ((64, 64, 64), 1, 0.28, 5), ((300, 257), 0, 0.55, 6)]
+CASES = [((40, 33), 0, 0.6, 1, ()), ((29, 41), 1, 0.58, 2, ()), ((23, 19, 17), 0, 0.36, 3, ()),
+         ((18, 21, 20), 2, 0.34, 4, ()), ((64, 64, 64), 1, 0.28, 5, ()), ((300, 257), 0, 0.55, 6, ()),
+         ((45, 38), 0, 0.58, 7, (1,)), ((21, 19, 18), 0, 0.33, 8, (1, 2)), ((3, 40, 37), 0, 0.6, 9, ()),
+         ((130, 5, 4), 0, 0.5, 10, ())]
 
 
-@pytest.mark.parametrize("dims,f,p,seed", CASES)
+def oracle_backbone(level, dims, planes, f, per):
+    if level == "trees":
+        return oracle.backbone(dims, planes, flow_axis=f, periodic=per)
+    return oracle.backbone_blocks(dims, planes, flow_axis=f, periodic=per)
+
+
+@pytest.mark.parametrize("dims,f,p,seed,per", CASES)
 @pytest.mark.parametrize("precision", [0, 1])
-def test_backbone_and_solution_match_oracle(ns, dims, f, p, seed, precision):
+@pytest.mark.parametrize("level", ["blocks", "trees"])
+def test_backbone_and_solution_match_oracle(ns, monkeypatch, dims, f, p, seed, per, precision, level):
+    if level == "trees":
+        monkeypatch.setenv("NETSOLVE_PRUNE", "trees")
     gen = netgen.rng(9500 + seed)
-    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), p, gen)
-    ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13)
-    bb_ref = oracle.backbone(dims, planes, flow_axis=f)
-    with ns.Network(dims, planes, flow_axis=f) as net:
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen, periodic=per), p, gen)
+    ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13, periodic=per)
+    bb_ref = oracle_backbone(level, dims, planes, f, per)
+    with ns.Network(dims, planes, flow_axis=f, periodic=per) as net:
         bb = net.backbone()
         r = net.solve(ns.make_opts(precision=precision))
         P = net.pressure()
@@ -95,6 +111,54 @@ def test_backbone_in_batch_and_queue(ns):
     for (dims, planes), r, (st, rq) in zip(specs, res, qres):
         ref = oracle.solve(dims, planes, tol=1e-13)
         assert st == ns.NET_OK and r.status == ns.NET_OK
-        assert r.n_solved == rq.n_solved == int(oracle.backbone(dims, planes).sum())
+        assert r.n_solved == rq.n_solved == int(oracle.backbone_blocks(dims, planes).sum())
         if ref.g_eff > 0:
             assert rel(r.g_eff, ref.g_eff) <= G_TOL and rel(rq.g_eff, ref.g_eff) <= G_TOL
+
+
+def test_loops_stripped_beyond_trees(ns, monkeypatch):
+    """At near-threshold disorder the block backbone is strictly smaller than
+    the tree-stripped set, and both give the same G and pressures."""
+    gen = netgen.rng(9800)
+    dims = (40, 36, 34)
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.3, gen)
+    with ns.Network(dims, planes) as net:
+        a = net.solve()
+        Pa = net.pressure()
+    monkeypatch.setenv("NETSOLVE_PRUNE", "trees")
+    with ns.Network(dims, planes) as net:
+        b = net.solve()
+        Pb = net.pressure()
+    assert a.n_solved < b.n_solved < b.n_active == a.n_active
+    assert a.n_solved == int(oracle.backbone_blocks(dims, planes).sum())
+    assert rel(a.g_eff, b.g_eff) <= G_TOL
+    assert np.max(np.abs(Pa - Pb)) <= 1e-7
+
+
+def test_hand_made_dead_end_loop(ns):
+    """The oracle's hand-made 9 x 7 network: two parallel paths, a dead-end
+    loop and a dead-end tree on stems, a branch into the outlet face."""
+    dims = (9, 7)
+    gx = np.zeros((7, 8))
+    gy = np.zeros((6, 9))
+    gx[3, :] = 1.0
+    gx[6, :] = 1.5
+    gy[2, 4] = 2.0
+    gx[2, 4] = gy[1, 5] = gx[1, 4] = gy[1, 4] = 2.0
+    gy[2, 2] = gy[1, 2] = gy[0, 2] = 3.0
+    gy[2, 7] = gx[2, 7] = 0.5
+    gy[5, 3] = 2.5
+    gx[5, 3] = gy[4, 4] = gx[4, 3] = gy[4, 3] = 2.5
+    want = np.zeros((7, 9), bool)
+    want[3, 1:8] = True
+    want[6, 1:8] = True
+    want[2, 7] = True
+    ref = oracle.solve(dims, [gx, gy], tol=1e-14)
+    with ns.Network(dims, [gx, gy]) as net:
+        bb = net.backbone()
+        r = net.solve()
+        P = net.pressure()
+    np.testing.assert_array_equal(bb, want)
+    assert r.n_solved == int(want.sum())
+    assert rel(r.g_eff, ref.g_eff) <= G_TOL
+    assert np.max(np.abs(P - ref.P)) <= 1e-7

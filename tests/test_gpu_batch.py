@@ -103,9 +103,10 @@ def test_batch_degenerate_members(ns):
     assert ns.solve_batch([]) == []
 
 
-def test_queue_results_match_solo(ns):
+def test_queue_results_match_solo_and_oracle(ns):
     """Requests finish at different steps and their networks are released at
-    once while others keep running (30 requests, 6 slots, 2D and 3D)."""
+    once while others keep running (30 requests, 6 slots, 2D and 3D); every
+    result equals the stand-alone solve and the oracle."""
     specs = mixed_nets(30, seed0=100)
     with ns.Queue(mem_budget_bytes=96 << 20, max_slots=6) as q:
         tickets = [q.submit(d, p) for d, p in specs]
@@ -115,10 +116,77 @@ def test_queue_results_match_solo(ns):
     for (dims, planes), (st, r) in zip(specs, results):
         assert st == ns.NET_OK, (st, r)
         s = solo(ns, dims, planes)
+        ref = oracle.solve(dims, planes, tol=1e-13)
         if s.g_eff == 0.0:
-            assert r.g_eff == 0.0
+            assert r.g_eff == 0.0 and ref.g_eff == 0.0
         else:
             assert rel(r.g_eff, s.g_eff) <= G_TOL
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL
+
+
+def test_queue_admits_requests_while_others_run(ns):
+    """Continuous batching: a slow request (a 2048^2 network near the 2D
+    percolation threshold) is admitted first; small requests that arrive
+    while it runs are admitted onto the device beside it (co_running >= 1,
+    with a measured wait), and every result matches the oracle (the slow one
+    its stand-alone solve)."""
+    import time
+
+    gen = netgen.rng(6200)
+    big_dims = (2048, 2048)
+    big = (big_dims, netgen.percolate(netgen.lognormal_iid(big_dims, gen, 1.0), 0.53, gen))
+    smalls = [netgen.batch_instance(400 + i, smin=40, smax=120) for i in range(6)]
+    with ns.Queue(mem_budget_bytes=8 << 30, max_slots=8) as q:
+        tb = q.submit(*big)
+        time.sleep(0.1)
+        ts = []
+        for d, p in smalls:
+            ts.append(q.submit(d, p))
+            time.sleep(0.01)
+        small_res = [q.wait(t, timeout_ms=120000) for t in ts]
+        big_res = q.wait(tb, timeout_ms=300000)
+    assert big_res[0] == ns.NET_OK, big_res
+    assert big_res[1].co_running == 0
+    beside = [r.co_running for _, r in small_res]
+    assert max(beside) >= 1, beside  # admitted while the slow one was on the device
+    for (dims, planes), (st, r) in zip(smalls, small_res):
+        assert st == ns.NET_OK, (st, r)
+        assert r.queue_ms >= 0.0
+        ref = oracle.solve(dims, planes, tol=1e-13)
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL
+    a = solo(ns, *big)
+    assert rel(big_res[1].g_eff, a.g_eff) <= G_TOL
+
+
+def test_batch_wide_members_match_oracle(ns):
+    """Members as wide as the 512-network workload's widest (1024, 760 and
+    540 columns: sweep stages of only two or three rows) beside small ones,
+    lognormal and percolated: every member's G_eff and pressures against the
+    oracle."""
+    shapes = [(1024, 48), (760, 40), (540, 64), (96, 80), (33, 150), (1024, 9)]
+    specs = []
+    for i, dims in enumerate(shapes):
+        gen = netgen.rng(6100 + i)
+        planes = netgen.lognormal_iid(dims, gen, 1.0)
+        if i % 2:
+            planes = netgen.percolate(planes, 0.6, gen)
+        specs.append((dims, planes))
+    nets = [ns.Network(d, p) for d, p in specs]
+    res = ns.solve_batch(nets)
+    for (dims, planes), net, r in zip(specs, nets, res):
+        assert r.status == ns.NET_OK, (dims, r)
+        ref = oracle.solve(dims, planes, tol=1e-13)
+        P = net.pressure()
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL, (dims, r.g_eff, ref.g_eff)
+        assert np.max(np.abs(P - ref.P)) <= 1e-7, dims
+    for net in nets:
+        net.close()
 
 
 def test_queue_budget_cancel_and_errors(ns):

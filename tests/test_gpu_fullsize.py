@@ -56,6 +56,23 @@ def test_fbm2048_against_stored_oracle(ns, name, variant, f, precision):
     assert rel(r.energy_g, r.g_eff) <= 1e-8
 
 
+def test_fbm2048_pressures_against_stored_oracle(ns):
+    """Pressures of the 2048^2 headline network (persistent kernel over all
+    152 SMs, L2 set-aside) at 64 x 64 sampled nodes, element by element
+    against the oracle's stored values."""
+    ref = stored("fbm2048_iso_x")
+    if "P_sample" not in ref:
+        pytest.skip("no stored oracle pressures")
+    smp = ref["P_sample"]
+    dims, planes = netgen.workload_fbm2d(variant="isotropic")
+    with ns.Network(dims, planes) as net:
+        r = net.solve()
+        P = net.pressure()
+    assert r.status == ns.NET_OK
+    got = P[np.ix_(smp["rows"], smp["cols"])]
+    assert np.max(np.abs(got - np.array(smp["values"]))) <= 1e-7
+
+
 def test_fbm2048_layered_closed_forms(ns):
     """Noise-free layers: arithmetic mean along, harmonic mean across."""
     dims, planes = netgen.workload_fbm2d(variant="stratified_exact")
@@ -78,6 +95,16 @@ def test_perc256_labels_bit_exact(ns):
         lab, cls = net.labels()
     np.testing.assert_array_equal(cls, cls_ref)
     np.testing.assert_array_equal(lab, lab_ref)
+
+
+def test_perc256_backbone_bit_exact(ns):
+    """The current-carrying backbone of the 256^3 network (dead-end trees and
+    loops removed), bit for bit against the oracle's Hopcroft-Tarjan blocks."""
+    dims, planes = netgen.workload_perc3d()
+    want = oracle.backbone_blocks(dims, planes)
+    with ns.Network(dims, planes) as net:
+        bb = net.backbone()
+    np.testing.assert_array_equal(bb, want)
 
 
 def test_perc256_solve(ns):

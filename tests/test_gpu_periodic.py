@@ -51,7 +51,7 @@ def test_periodic_matches_oracle(ns, monkeypatch, dims, f, per, p, seed, precisi
     planes = periodic_net(dims, per, p, seed)
     ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13, periodic=per)
     lab_o, cls_o = oracle.labels(dims, planes, flow_axis=f, periodic=per)
-    bb_o = oracle.backbone(dims, planes, f, periodic=per)
+    bb_o = oracle.backbone_blocks(dims, planes, f, periodic=per)
     with ns.Network(dims, planes, flow_axis=f, periodic=per) as net:
         r = net.solve(ns.make_opts(precision=precision, refine=refine))
         P = net.pressure()
