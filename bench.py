@@ -56,6 +56,9 @@ def args_():
                     help="fbmgen: log2 of the node counts (even), comma separated")
     ap.add_argument("--aniso-size", type=int, default=512)
     ap.add_argument("--aniso-real", type=int, default=8)
+    ap.add_argument("--aniso-bc", default="periodic", choices=["periodic", "noflow"],
+                    help="aniso: transverse faces periodic (the paper's, Sec. II; K_y from the "
+                         "transposed field) or no-flow")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -649,9 +652,16 @@ def serve_line(a, n_sat, fracs, n_sweep):
             counts[name] = counts.get(name, 0) + 1
         errors = sorted({r.error for st, r in results if st != 0 and r is not None})[:4]
         worst = max((r.g_eff_err for st, r in results if st == 0 and r is not None), default=None)
+        waits = sorted(r.queue_ms for st, r in results if r is not None)
+        beside = sum(1 for st, r in results if r is not None and r.co_running > 0)
+
+        def pct(v, f):
+            return v[min(len(v) - 1, int(f * (len(v) - 1) + 0.5))] if v else None
+
         return {"offered_rate": rate, "requests": n, "ok": ok, "status_counts": counts, "errors": errors,
                 "solves_per_s": n / (t1 - t0), "p50_ms": p50, "p99_ms": p99, "wall_s": t1 - t0,
-                "max_g_eff_err_estimate": worst}
+                "queue_wait_p50_ms": pct(waits, 0.5), "queue_wait_p99_ms": pct(waits, 0.99),
+                "admitted_beside_running": beside, "max_g_eff_err_estimate": worst}
 
     run(50.0, 16)  # warm-up
     with Clocks(0) as clk:
@@ -686,10 +696,15 @@ def run_aniso(a):
     ns.lib(build_if_missing=True)
     n, R = a.aniso_size, a.aniso_real
     cells, total_s, solves, worst = [], 0.0, 0, 0.0
+    per = a.aniso_bc == "periodic"
     for hi, H in enumerate(netgen.ANISO_H):
         for ri, ratio in enumerate(netgen.ANISO_RATIOS):
-            specs = [netgen.aniso_instance(hi, ri, r, n=n) for r in range(R)]
-            nets = [ns.Network(d, p, flow_axis=ax) for d, p in specs for ax in (0, 1)]
+            if per:  # both axes as flow along x with periodic y: the field and its transpose
+                nets = [ns.Network(d, p, periodic=(1,)) for r in range(R)
+                        for d, p in netgen.aniso_pair_periodic(hi, ri, r, n=n)]
+            else:
+                specs = [netgen.aniso_instance(hi, ri, r, n=n) for r in range(R)]
+                nets = [ns.Network(d, p, flow_axis=ax) for d, p in specs for ax in (0, 1)]
             t = time.perf_counter()
             res = ns.solve_batch(nets, ns.make_opts(tol_rel=TOL_REL))
             total_s += time.perf_counter() - t
@@ -707,7 +722,9 @@ def run_aniso(a):
     line = {"metric": METRIC, "workload": "aniso", "value": solves / total_s, "unit": "solves/s",
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{n}x{n} anisotropic FBM networks (Eq. 2), sigma=1, {R} realizations "
-                                   "per (H, beta_x/beta_y), K_x and K_y batched", "tol_rel": TOL_REL},
+                                   "per (H, beta_x/beta_y), K_x and K_y batched; transverse faces "
+                                   + ("periodic (K_y from the transposed field)" if per else "no-flow"),
+                       "tol_rel": TOL_REL},
             "solves": solves, "seconds": total_s, "max_geff_err_estimate": worst, "cells": cells,
             "paper_ranges": {"H=0.75": [0.6, 1.6], "H=0.35": [0.5, 2.5],
                              "note": "Fig. 10 bounds (3.6M-node networks); context only"}}

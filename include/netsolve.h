@@ -100,10 +100,14 @@ typedef struct {
     unsigned periodic_mask;  /* bit d set: axis d is periodic (Sec. II); only
                                 y (bit 1) and z (bit 2), never the flow axis,
                                 each with n[d] >= 3.  0: no-flow boundaries.
-                                Periodic networks are solved by net_solve
-                                (the compacted CG); net_solve_batch, netq_*,
-                                net_autotune and net_labels_noalloc reject
-                                them with NET_EINVAL. */
+                                Periodic networks are solved on their list
+                                of unknowns (whose table holds the wrap
+                                bonds) or, dense 2D ones alone, by the
+                                persistent kernel; net_solve, net_solve_batch
+                                and netq_* take them, net_autotune (which
+                                tunes the lattice sweep) and
+                                net_labels_noalloc reject them with
+                                NET_EINVAL. */
     double p_in, p_out;      /* face pressures, finite, p_in != p_out */
     int bond_dtype;          /* NET_F64 or NET_F32 */
     int on_device;           /* 1: bond pointers are device pointers on the
@@ -345,8 +349,11 @@ net_status net_fbm_bonds(const net_desc *desc, const double *field, double sigma
  * (Sec. IV) is one launch of a kernel with one CTA per SM that walks all
  * running networks' segments; each network keeps its own CG scalars and its
  * own convergence mask, and networks drop out as they converge while the
- * rest continue.  The sweeps run as CUDA-graph chunks of opts->check_every
- * launches (0 = 16).  res[i] receives network i's result; each result
+ * rest continue.  Networks whose unknowns are under 35 % of their lattice
+ * (near-critical percolation after dead-end stripping) and periodic networks
+ * are solved on their lists of unknowns instead: one launch per phase of the
+ * iteration for all of them, the lists cut into segments.  The sweeps run as
+ * CUDA-graph chunks of opts->check_every iterations (0 = 16).  res[i] receives network i's result; each result
  * matches the network's stand-alone net_solve within the solver tolerance.
  * All networks must live on the current device.  opts NULL = defaults (one
  * opts for all; x0 is ignored).  Returns NET_OK if every network converged,

@@ -30,6 +30,7 @@ __global__ void gather_status_kernel(const InnerScal *const *s, int n, int *stop
 __global__ void set_stop_kernel(InnerScal *s, int v) { s->stop = v; }
 
 __global__ void retire_kernel(SweepInst *inst, int idx, InnerScal *dead) { inst[idx].s = dead; }
+__global__ void retire_compact_kernel(CompactInst *inst, int idx, InnerScal *dead) { inst[idx].a.s = dead; }
 
 #define CKB(call)                                                \
     do {                                                         \
@@ -55,11 +56,13 @@ BatchEngine::BatchEngine(int device, cudaStream_t stream) : device_(device), st_
     nsm_ = 0;
     if (cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm_ <= 0)
         nsm_ = 152;
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) {
-            groups_[d][f].ndim = d + 2;
-            groups_[d][f].f32 = f;
-        }
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) {
+                groups_[c][d][f].ndim = d + 2;
+                groups_[c][d][f].f32 = f;
+                groups_[c][d][f].compact = c == 1;
+            }
     InnerScal dead{};
     dead.stop = 1;
     if (cudaMallocAsync((void **)&dead_, sizeof(InnerScal), st_) == cudaSuccess)
@@ -70,21 +73,27 @@ BatchEngine::BatchEngine(int device, cudaStream_t stream) : device_(device), st_
 void BatchEngine::retire(Group &g, BatchItem *it) {
     for (size_t k = 0; k < g.planned.size(); k++)
         if (g.planned[k] == it) {
-            retire_kernel<<<1, 1, 0, st_>>>(g.d_inst, (int)k, dead_);
+            if (g.compact)
+                retire_compact_kernel<<<1, 1, 0, st_>>>(g.d_cinst, (int)k, dead_);
+            else
+                retire_kernel<<<1, 1, 0, st_>>>(g.d_inst, (int)k, dead_);
             g.planned[k] = nullptr;
         }
 }
 
 BatchEngine::~BatchEngine() {
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) {
-            Group &g = groups_[d][f];
-            if (g.exec) cudaGraphExecDestroy(g.exec);
-            dfree(g.d_inst, st_);
-            dfree(g.d_segs, st_);
-            dfree(g.d_cta, st_);
-            dfree(g.d_part, st_);
-        }
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) {
+                Group &g = groups_[c][d][f];
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                dfree(g.d_inst, st_);
+                dfree(g.d_segs, st_);
+                dfree(g.d_cta, st_);
+                dfree(g.d_part, st_);
+                dfree(g.d_cinst, st_);
+                dfree(g.d_csegs, st_);
+            }
     dfree((void *)d_sptr_, st_);
     dfree(d_stop_, st_);
     dfree(d_iter_, st_);
@@ -93,6 +102,7 @@ BatchEngine::~BatchEngine() {
 }
 
 net_status BatchEngine::outer_pass(BatchItem *it, int apply_corr, int corr_f32) {
+    if (it->compact) return outer_pass_compact(it->net, it->f32, apply_corr, it->opts, st_);
     OuterArgs oa = outer_args(it->net, it->f32, apply_corr, corr_f32, it->opts);
     CKB(launch_outer(oa, st_));
     return NET_OK;
@@ -130,8 +140,9 @@ void BatchEngine::finish(BatchItem *it, net_status st) {
     // no more sweeps for this network, whatever plan it is still part of
     set_stop_kernel<<<1, 1, 0, st_>>>(&n->dsc->in[0], 1);
     set_stop_kernel<<<1, 1, 0, st_>>>(&n->dsc->in[1], 1);
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) retire(groups_[d][f], it);
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) retire(groups_[c][d][f], it);
     it->done = true;
     done_.push_back(it);
 }
@@ -165,6 +176,11 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
         CKB(cudaStreamWaitEvent(st_, n->ev[3], 0));
         net_status s = ensure_precision(n, it->f32, st_);
         if (s != NET_OK) return s;
+        it->compact = batch_takes_compact(n, it->f32);
+        if (it->compact) {
+            s = prepare_compact(n, it->f32, st_);
+            if (s != NET_OK) return s;
+        }
         const void *gr[3] = {n->graw[0], n->graw[1], n->g.ndim == 3 ? n->graw[2] : n->graw[0]};
         CKB(launch_build_system(n->g, gr, n->raw_f32, n->cls, n->dis, n->x, &n->dsc->ss, n->partials, st_));
         s = outer_pass(it, 0, it->f32);
@@ -181,7 +197,7 @@ net_status BatchEngine::add(const std::vector<BatchItem *> &items) {
             finish(it, NET_OK);
             continue;
         }
-        Group &g = group_of(n->g.ndim, it->f32);
+        Group &g = group_of(n->g.ndim, it->f32, it->compact);
         g.items.push_back(it);
         g.dirty = true;
         nrun_++;
@@ -280,42 +296,92 @@ net_status BatchEngine::rebuild(Group &g, int K) {
     return NET_OK;
 }
 
+net_status BatchEngine::rebuild_compact(Group &g, int K) {
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    std::vector<CompactInst> ci(g.items.size());
+    std::vector<CompactSeg> segs;
+    size_t tot_part = 0;
+    std::vector<size_t> off(g.items.size());
+    for (size_t k = 0; k < g.items.size(); k++) {
+        const long long U = compact_args_of(g.items[k]->net, g.f32).n;
+        const int ns = (int)std::max(1LL, (U + COMPACT_SEG - 1) / COMPACT_SEG);
+        off[k] = tot_part;
+        tot_part += (size_t)ns * 4;
+        for (int j = 0; j < ns; j++)
+            segs.push_back(CompactSeg{(int)k, (int)(U * j / ns), (int)(U * (j + 1) / ns), j});
+        ci[k].nseg = ns;
+    }
+    CKB(grow(&g.d_cinst, &g.cap_cinst, ci.size(), st_));
+    CKB(grow(&g.d_csegs, &g.cap_csegs, segs.size(), st_));
+    CKB(grow(&g.d_part, &g.cap_part, tot_part, st_));
+    for (size_t k = 0; k < g.items.size(); k++) {
+        ci[k].a = compact_args_of(g.items[k]->net, g.f32);
+        ci[k].part = g.d_part + off[k];
+    }
+    CKB(cudaMemcpyAsync(g.d_cinst, ci.data(), sizeof(CompactInst) * ci.size(), cudaMemcpyHostToDevice, st_));
+    CKB(cudaMemcpyAsync(g.d_csegs, segs.data(), sizeof(CompactSeg) * segs.size(), cudaMemcpyHostToDevice, st_));
+    cudaStream_t cs;
+    CKB(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int i = 0; e == cudaSuccess && i < K; i++)
+        e = launch_compact_batch(g.ndim, g.f32, g.d_cinst, g.d_csegs, (int)segs.size(), cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph (compacted)");
+    CKB(cudaStreamSynchronize(st_));
+    g.nseg = (int)segs.size();
+    g.K = K;
+    g.dirty = false;
+    g.planned = g.items;
+    return NET_OK;
+}
+
 net_status BatchEngine::step(int K) {
     if (nrun_ == 0) return NET_OK;
     const bool tr = trace_on();
     const auto t0 = std::chrono::steady_clock::now();
     if (tr) {
         // running networks and unknowns per group before this step
+        for (int c = 0; c < 2; c++)
+            for (int d = 0; d < 2; d++)
+                for (int f = 0; f < 2; f++) {
+                    const Group &g = groups_[c][d][f];
+                    if (g.items.empty()) continue;
+                    long long u = 0;
+                    for (const BatchItem *it : g.items) u += it->net->n_solved;
+                    fprintf(stderr, "[trace batch-step %dD %s %s] running %zu unknowns %lld K %d\n", d + 2,
+                            f ? "f32" : "f64", c ? "list" : "lattice", g.items.size(), u, K);
+                }
+    }
+    for (int c = 0; c < 2; c++)
         for (int d = 0; d < 2; d++)
             for (int f = 0; f < 2; f++) {
-                const Group &g = groups_[d][f];
+                Group &g = groups_[c][d][f];
                 if (g.items.empty()) continue;
-                long long u = 0;
-                for (const BatchItem *it : g.items) u += it->net->n_active;
-                fprintf(stderr, "[trace batch-step %dD %s] running %zu unknowns %lld K %d\n", d + 2,
-                        f ? "f32" : "f64", g.items.size(), u, K);
+                if (g.dirty || g.K != K || !g.exec) {
+                    net_status s = g.compact ? rebuild_compact(g, K) : rebuild(g, K);
+                    if (s != NET_OK) return s;
+                }
+                CKB(cudaGraphLaunch(g.exec, st_));
+                g.swept = true;
             }
-    }
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) {
-            Group &g = groups_[d][f];
-            if (g.items.empty()) continue;
-            if (g.dirty || g.K != K || !g.exec) {
-                net_status s = rebuild(g, K);
-                if (s != NET_OK) return s;
-            }
-            CKB(cudaGraphLaunch(g.exec, st_));
-            g.swept = true;
-        }
     // one read of every running network's stop flag and iteration count
     std::vector<BatchItem *> run;
     std::vector<const InnerScal *> ptrs;
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++)
-            for (BatchItem *it : groups_[d][f].items) {
-                run.push_back(it);
-                ptrs.push_back(&it->net->dsc->in[it->f32 ? 0 : 1]);
-            }
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++)
+                for (BatchItem *it : groups_[c][d][f].items) {
+                    run.push_back(it);
+                    ptrs.push_back(&it->net->dsc->in[it->f32 ? 0 : 1]);
+                }
     const size_t n = run.size();
     if (cap_g_ < n) {
         dfree((void *)d_sptr_, st_);
@@ -381,16 +447,21 @@ net_status BatchEngine::step(int K) {
         set_stop_kernel<<<1, 1, 0, st_>>>(&nt->dsc->in[0], 1);
         net_status s = ensure_precision(nt, 0, st_);
         if (s != NET_OK) return s;
-        Group &g32 = group_of(nt->g.ndim, 1);
+        Group &g32 = group_of(nt->g.ndim, 1, it->compact);
         g32.items.erase(std::remove(g32.items.begin(), g32.items.end(), it), g32.items.end());
         retire(g32, it);
         g32.dirty = true;
         it->f32 = 0;
         it->fallback = 1;
+        it->compact = batch_takes_compact(nt, 0);
+        if (it->compact) {
+            s = prepare_compact(nt, 0, st_);
+            if (s != NET_OK) return s;
+        }
         s = outer_pass(it, 0, 0);
         if (s != NET_OK) return s;
         it->prog.start(it->rel, geff_err(nt));
-        Group &g64 = group_of(nt->g.ndim, 0);
+        Group &g64 = group_of(nt->g.ndim, 0, it->compact);
         g64.items.push_back(it);
         g64.dirty = true;
     }
@@ -398,18 +469,20 @@ net_status BatchEngine::step(int K) {
     // its busiest CTA, and the CTAs that held a finished network's segments
     // would otherwise idle while the rest keep their full share.  A replan
     // (host cut, upload, graph instantiation) costs far less than a step.
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) {
-            Group &g = groups_[d][f];
-            const size_t before = g.items.size();
-            g.items.erase(std::remove_if(g.items.begin(), g.items.end(), [](BatchItem *it) { return it->done; }),
-                          g.items.end());
-            if (before != g.items.size()) g.dirty = true;
-            if (g.items.empty()) g.swept = false;
-        }
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) {
+                Group &g = groups_[c][d][f];
+                const size_t before = g.items.size();
+                g.items.erase(std::remove_if(g.items.begin(), g.items.end(), [](BatchItem *it) { return it->done; }),
+                              g.items.end());
+                if (before != g.items.size()) g.dirty = true;
+                if (g.items.empty()) g.swept = false;
+            }
     nrun_ = 0;
-    for (int d = 0; d < 2; d++)
-        for (int f = 0; f < 2; f++) nrun_ += groups_[d][f].items.size();
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 2; d++)
+            for (int f = 0; f < 2; f++) nrun_ += groups_[c][d][f].items.size();
     return NET_OK;
 }
 
@@ -438,10 +511,6 @@ NET_API net_status net_solve_batch(net_t *const *nets, int count, const net_opts
     for (int i = 0; i < count; i++) {
         if (!nets[i] || nets[i]->device != dev) {
             set_error("net_solve_batch: network %d is NULL or on another device", i);
-            return NET_EINVAL;
-        }
-        if (nets[i]->g.per) {
-            set_error("net_solve_batch: network %d is periodic; solve it with net_solve", i);
             return NET_EINVAL;
         }
     }

@@ -1,9 +1,12 @@
 // batch.h -- many networks solved together (internal).
 //
 // The engine keeps a set of networks whose refinement loops are in flight.
-// Networks are grouped by (dimension, inner precision); each group has one
-// sweep plan (all its running networks' segments dealt over the SMs) and a
-// CUDA graph of K sweep launches.  step() replays every group's graph once,
+// Networks are grouped by (path, dimension, inner precision).  On the lattice
+// path each group has one sweep plan (all its running networks' segments
+// dealt over the SMs) and a CUDA graph of K sweep launches; on the compacted
+// path (networks whose unknowns are a small part of the lattice, and periodic
+// networks) a group's networks are cut into list segments and its graph holds
+// K pairs of phase launches over all of them.  step() replays every group's graph once,
 // gathers all stop flags with one small kernel and one read, and runs the
 // FP64 outer pass of every network whose inner solve stopped; those
 // networks then continue, switch to FP64, or finish.  Finished networks
@@ -23,6 +26,7 @@ struct BatchItem {
     net_t *net = nullptr;
     net_opts opts{};
     int f32 = 1;             // inner precision in use
+    bool compact = false;    // solved on its list of unknowns
     int outer = 0;
     long long inner_total = 0;
     double rel = 0.0;
@@ -52,6 +56,11 @@ public:
 private:
     struct Group {
         int ndim = 2, f32 = 1;
+        bool compact = false;              // the compacted path
+        CompactInst *d_cinst = nullptr;    // compacted path: networks, segments
+        CompactSeg *d_csegs = nullptr;
+        size_t cap_cinst = 0, cap_csegs = 0;
+        int nseg = 0;
         std::vector<BatchItem *> items;
         bool dirty = true;
         SweepInst *d_inst = nullptr;
@@ -71,18 +80,19 @@ private:
     // replan.
     void retire(Group &g, BatchItem *it);
     net_status rebuild(Group &g, int K);
+    net_status rebuild_compact(Group &g, int K);
     // Tile shape for the group's next plan: the tuned entry of its key; else,
     // while no sweep has run on the group (its state is freshly armed), tune
     // now and re-arm; else the nearest tuned size class; else the default.
     net_status choose_shape(Group &g, PlanShape *shape);
     net_status outer_pass(BatchItem *it, int apply_corr, int corr_f32);
     void finish(BatchItem *it, net_status st);
-    Group &group_of(int ndim, int f32) { return groups_[ndim - 2][f32 ? 1 : 0]; }
+    Group &group_of(int ndim, int f32, bool compact) { return groups_[compact ? 1 : 0][ndim - 2][f32 ? 1 : 0]; }
 
     int device_;
     int nsm_;
     cudaStream_t st_;
-    Group groups_[2][2];
+    Group groups_[2][2][2];  // [compacted path][dimension - 2][FP32 inner]
     size_t nrun_ = 0;
     std::vector<BatchItem *> done_;
     // stop-flag gather

@@ -33,9 +33,11 @@
 namespace netsolve {
 namespace {
 
-constexpr int CT = 512;                 // threads per CTA
+constexpr int CT = 512;                 // threads per CTA (batched phases)
 constexpr int CW = CT / 32;
-constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP64; more spill)
+constexpr int CTC = 512;                // threads per CTA of the cooperative solve (two per SM: one
+constexpr int CWC = CTC / 32;           //   1024-thread CTA per SM measured slower, 28.7 against 26.5 us)
+constexpr int UNR = 2;                  // unknowns a thread keeps in flight (FP64)
 constexpr int UNR32 = 2;                // the same in FP32
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
 
@@ -178,11 +180,9 @@ __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------ refinement glue
-// The armed residual is r_{iter-1}: it goes into set (iter + 1) & 1.
 template <typename T>
 __global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx, const T *__restrict__ src,
-                                      T *r0, T *r1, const InnerScal *is) {
-    T *dst = (is->iter & 1) ? r0 : r1;
+                                      T *dst) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
          k += (long long)gridDim.x * blockDim.x)
         dst[k] = src[cidx[k]];
@@ -192,11 +192,9 @@ __global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx,
 // alpha_k p_k (the recursion continues): fold it in and clear y.
 template <typename T>
 __global__ void compact_correct_kernel(long long U, const int *__restrict__ cidx, const double *__restrict__ dis,
-                                       double *x, T *y, const T *p0, const T *p1, const InnerScal *is) {
+                                       double *x, T *y, const T *__restrict__ p, const InnerScal *is) {
     const bool owe = is->stop == 6;
     const double a = is->alpha;
-    // the last iteration k = iter - 1 wrote p_k into set k & 1
-    const T *__restrict__ p = (is->iter & 1) ? p0 : p1;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
          k += (long long)gridDim.x * blockDim.x) {
         double d = (double)y[k];
@@ -255,37 +253,104 @@ __device__ __forceinline__ void barrier_release(unsigned *gen, unsigned target) 
     st_release_u32(gen, target);
 }
 
-// Iteration k (st.iter) reads r_{k-1}, p_{k-1}, q_{k-1} from set (k+1)&1 and
-// writes r_k, p_k, q_k into set k&1 (the armed residual is r_{-1}, in set 1
-// at a fresh start).  CTA c owns the contiguous list range [u0, u1); its p_k
-// is also kept in shared memory (when the range fits) for the operator.
-// A neighbour outside the range is another CTA's: its p_k is formed here from
-// that CTA's r_{k-1}, q_{k-1}, p_{k-1}, which nobody writes during
-// iteration k -- so one grid barrier per iteration suffices.
-template <typename T>
-struct PrevSet {
-    const T *r, *p, *q;
-    T alpha, beta;
-    bool first;
-    __device__ __forceinline__ T p_of(int j) const {
-        const T rj = __ldcg(r + j);
-        if (first) return rj;
-        return fma(beta, __ldcg(p + j), fma(-alpha, __ldcg(q + j), rj));
+// Phase A of iteration k on the list entries k = kb, kb + st, ... < ke:
+// finish iteration k-1 (r -= alpha q; y += alpha p; p = r + beta p), or at
+// the first iteration p = r, y = 0.  UN entries in flight per thread.
+template <typename T, int UN>
+__device__ __forceinline__ void compact_phase_a(T *__restrict__ y, T *__restrict__ r, T *p, const T *__restrict__ q,
+                                                int kb, int ke, int st, T alpha, T beta, bool first) {
+    for (int k0 = kb; k0 < ke; k0 += UN * st) {
+        T rk[UN], pk[UN], qk[UN], yk[UN];
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int k = k0 + u * st;
+            if (k < ke) {
+                rk[u] = r[k];
+                if (!first) {
+                    pk[u] = p[k];
+                    qk[u] = q[k];
+                    yk[u] = y[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int k = k0 + u * st;
+            if (k >= ke) continue;
+            if (first) {
+                p[k] = rk[u];
+                y[k] = T(0);
+            } else {
+                const T rn = fma(-alpha, qk[u], rk[u]);
+                r[k] = rn;
+                y[k] = fma(alpha, pk[u], yk[u]);
+                p[k] = fma(beta, pk[u], rn);
+            }
+        }
     }
-};
+}
+
+// Phase B on the entries k = kb, kb + st, ... < ke of a list of U unknowns:
+// q = A p (neighbours' p read through L2) and this thread's share of
+// <p,q>, <r,q>, <q,q>, <r,r>.
+template <typename T, int NDIM, int UN>
+__device__ __forceinline__ void compact_phase_b(const T *__restrict__ r, const T *p, T *__restrict__ q,
+                                                const T *__restrict__ val, const int *__restrict__ nbr, int U,
+                                                int kb, int ke, int st, T &s_pq, T &s_rq, T &s_qq, T &s_rr) {
+    const long long VS = U + 1;  // val slot stride
+    for (int k0 = kb; k0 < ke; k0 += UN * st) {
+        T wxp[UN], wxm[UN], wp[UN][NDIM - 1];
+        int ip[UN][NDIM - 1], im[UN][NDIM - 1];
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int k = k0 + u * st;
+            const bool ok = k < ke;
+            const int kk = ok ? k : 0;
+            wxp[u] = ok ? __ldg(val + kk) : T(0);
+            wxm[u] = (ok && k > 0) ? __ldg(val + kk - 1) : T(0);
+#pragma unroll
+            for (int d = 1; d < NDIM; d++) {
+                wp[u][d - 1] = ok ? __ldg(val + d * VS + kk) : T(0);
+                ip[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1)) * U + kk) : (int)kk;
+                im[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + kk) : ~(int)kk;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int k = k0 + u * st;
+            if (k >= ke) continue;
+            const T pk = __ldcg(p + k);
+            T nb = wxp[u] * __ldcg(p + k + 1);
+            nb = fma(wxm[u], __ldcg(p + (k > 0 ? k - 1 : 0)), nb);
+#pragma unroll
+            for (int d = 1; d < NDIM; d++) {
+                nb = fma(wp[u][d - 1], __ldcg(p + ip[u][d - 1]), nb);
+                const int jm = im[u][d - 1];
+                const int jj = jm >= 0 ? jm : ~jm;
+                const T wm = jm >= 0 ? __ldg(val + d * VS + jj) : T(0);
+                nb = fma(wm, __ldcg(p + jj), nb);
+            }
+            const T qk = pk - nb;
+            q[k] = qk;
+            const T rk = r[k];
+            s_pq = fma(pk, qk, s_pq);
+            s_rq = fma(rk, qk, s_rq);
+            s_qq = fma(qk, qk, s_qq);
+            s_rr = fma(rk, rk, s_rr);
+        }
+    }
+}
 
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
-    extern __shared__ __align__(16) unsigned char dyn[];
-    T *sp = reinterpret_cast<T *>(dyn);  // p_k of this CTA's range (when it fits)
+__global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
     __shared__ InnerScal st;
-    __shared__ T s_red[CW][4];
+    __shared__ T s_red[CWC][4];
     const int G = gridDim.x, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *__restrict__ y = (T *)a.y;
-    T *rs[2] = {(T *)a.r, (T *)a.r2};
-    T *ps[2] = {(T *)a.p, (T *)a.p2};
-    T *qs[2] = {(T *)a.q, (T *)a.q2};
+    T *__restrict__ r = (T *)a.r;
+    T *p = (T *)a.p;
+    T *__restrict__ q = (T *)a.q;
     const T *__restrict__ val = (const T *)a.val;
     const int *__restrict__ nbr = a.nbr;
     unsigned *bar_count = a.bar, *bar_gen = a.bar + 1;
@@ -296,102 +361,26 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
     }
     __syncthreads();
     // list indices fit in 32 bits (the table stores them as int)
+    const int tid = c * CTC + (int)threadIdx.x, nth = G * CTC;
     const int U = (int)a.n;
-    const int u0 = (int)((long long)U * c / G), u1 = (int)((long long)U * (c + 1) / G);
-    const bool staged = u1 - u0 <= a.stage_cap;
     constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
-    constexpr int STEP = UN * CT;
-    const long long VS = U + 1;  // val slot stride
     unsigned target = 0;
+    bool bad = false;
     while (st.stop == 0) {
         const bool first = st.iter == 0;
         const T alpha = (T)st.alpha, beta = (T)st.beta;
-        const int cur = (int)(st.iter & 1), prv = cur ^ 1;
-        T *__restrict__ rn = rs[cur];
-        T *__restrict__ pn = ps[cur];
-        T *__restrict__ qn = qs[cur];
-        const PrevSet<T> old{rs[prv], ps[prv], qs[prv], alpha, beta, first};
-        // ---- phase A: finish iteration k-1 on the own range ----
-        for (int k0 = u0 + (int)threadIdx.x; k0 < u1; k0 += STEP) {
-            T rk[UN], pk[UN], qk[UN], yk[UN];
-#pragma unroll
-            for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * CT;
-                if (k < u1) {
-                    rk[u] = old.r[k];
-                    if (!first) {
-                        pk[u] = old.p[k];
-                        qk[u] = old.q[k];
-                        yk[u] = y[k];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * CT;
-                if (k >= u1) continue;
-                T r1 = rk[u], p1 = rk[u];
-                if (first) {
-                    y[k] = T(0);
-                } else {
-                    r1 = fma(-alpha, qk[u], rk[u]);
-                    p1 = fma(beta, pk[u], r1);
-                    y[k] = fma(alpha, pk[u], yk[u]);
-                }
-                rn[k] = r1;
-                pn[k] = p1;
-                if (staged) sp[k - u0] = p1;
-            }
+        // ---- phase A: finish iteration k-1 (UN unknowns in flight per thread) ----
+        compact_phase_a<T, UN>(y, r, p, q, tid, U, nth, alpha, beta, first);
+        ++target;
+        if (barrier_arrive(bar_count, target, G, target == 1u && c == a.skip_cta)) {
+            if (threadIdx.x == 0) barrier_release(bar_gen, target);
+        } else if (!barrier_wait(bar_gen, target, a.wait_ns)) {
+            bad = true;
         }
         __syncthreads();
-        // ---- phase B: q_k = A p_k and the four sums on the own range ----
+        // ---- phase B: q = A p and the four sums ----
         T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
-        auto pget = [&](int j) -> T {
-            if (j >= u0 && j < u1) return staged ? sp[j - u0] : __ldcg(pn + j);
-            return old.p_of(j);
-        };
-        for (int k0 = u0 + (int)threadIdx.x; k0 < u1; k0 += STEP) {
-            T wxp[UN], wxm[UN], wp[UN][NDIM - 1];
-            int ip[UN][NDIM - 1], im[UN][NDIM - 1];
-#pragma unroll
-            for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * CT;
-                const bool ok = k < u1;
-                const int kk = ok ? k : u0;
-                wxp[u] = ok ? __ldg(val + kk) : T(0);
-                wxm[u] = (ok && k > 0) ? __ldg(val + kk - 1) : T(0);
-#pragma unroll
-                for (int d = 1; d < NDIM; d++) {
-                    wp[u][d - 1] = ok ? __ldg(val + d * VS + kk) : T(0);
-                    ip[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1)) * U + kk) : kk;
-                    im[u][d - 1] = ok ? __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + kk) : ~kk;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UN; u++) {
-                const int k = k0 + u * CT;
-                if (k >= u1) continue;
-                const T pk = staged ? sp[k - u0] : __ldcg(pn + k);
-                T nb = wxp[u] != T(0) ? wxp[u] * pget(k + 1) : T(0);
-                if (wxm[u] != T(0)) nb = fma(wxm[u], pget(k - 1), nb);
-#pragma unroll
-                for (int d = 1; d < NDIM; d++) {
-                    if (wp[u][d - 1] != T(0)) nb = fma(wp[u][d - 1], pget(ip[u][d - 1]), nb);
-                    const int jm = im[u][d - 1];
-                    if (jm >= 0) {
-                        const T wm = __ldg(val + d * VS + jm);
-                        if (wm != T(0)) nb = fma(wm, pget(jm), nb);
-                    }
-                }
-                const T qk = pk - nb;
-                qn[k] = qk;
-                const T rk = __ldcg(rn + k);
-                s_pq = fma(pk, qk, s_pq);
-                s_rq = fma(rk, qk, s_rq);
-                s_qq = fma(qk, qk, s_qq);
-                s_rr = fma(rk, rk, s_rr);
-            }
-        }
+        compact_phase_b<T, NDIM, UN>(r, p, q, val, nbr, U, tid, U, nth, s_pq, s_rq, s_qq, s_rr);
         T t4[4] = {s_pq, s_rq, s_qq, s_rr};
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -401,18 +390,19 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
 #pragma unroll
             for (int k = 0; k < 4; k++) s_red[warp][k] = t4[k];
         __syncthreads();
-        const int par = cur;
+        const int par = (int)(st.iter & 1);
         if (threadIdx.x == 0) {
             double tot[4] = {0, 0, 0, 0};
-            for (int w = 0; w < CW; w++)
+            for (int w = 0; w < CWC; w++)
 #pragma unroll
                 for (int k = 0; k < 4; k++) tot[k] += (double)s_red[w][k];
+            if (bad) tot[0] = tot[1] = tot[2] = tot[3] = NAN;
 #pragma unroll
             for (int k = 0; k < 4; k++) a.pb[((long long)par * G + c) * 4 + k] = tot[k];
         }
         ++target;
         bool ok = true;
-        if (barrier_arrive(bar_count, target, G, target == 1u && c == a.skip_cta)) {
+        if (barrier_arrive(bar_count, target, G, false)) {
             // the last CTA: one warp sums the partials (lanes stride over
             // the CTAs, fixed order, FP64), advances the state, releases
             if (warp == 0) {
@@ -447,7 +437,7 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
                 }
             }
         }
-        if (threadIdx.x == 0 && !ok) {
+        if (threadIdx.x == 0 && (bad || !ok)) {
             atomicExch(a.err, 1);
             st.stop = 5;
         }
@@ -461,8 +451,76 @@ __global__ void __launch_bounds__(CT, 2) compact_cg_kernel(CompactArgs a) {
     }
 }
 
-// Shared memory for the staged p of a CTA's range (two CTAs per SM).
-constexpr int STAGE_BYTES = 64 * 1024;
+// ------------------------------------------------------------------ batches
+// Compacted networks inside a batch: one launch of each kernel per CG
+// iteration for every running network of the group (the kernel boundary is
+// the barrier between the phases), a network cut into segments of list
+// entries, one segment per CTA.  A network's last segment to finish phase B
+// sums the segments' partials in slot order (FP64) and runs finish_iteration,
+// as the lattice sweep does; stopped networks are skipped.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(CT) compact_batch_a_kernel(const CompactInst *__restrict__ insts,
+                                                             const CompactSeg *__restrict__ segs) {
+    const CompactSeg sg = segs[blockIdx.x];
+    const CompactInst &I = insts[sg.inst];
+    const InnerScal *s = I.a.s;
+    if (s->stop) return;
+    constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    compact_phase_a<T, UN>((T *)I.a.y, (T *)I.a.r, (T *)I.a.p, (const T *)I.a.q, sg.u0 + (int)threadIdx.x, sg.u1,
+                           CT, (T)s->alpha, (T)s->beta, s->iter == 0);
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(CT) compact_batch_b_kernel(const CompactInst *__restrict__ insts,
+                                                             const CompactSeg *__restrict__ segs) {
+    __shared__ T s_red[CW][4];
+    __shared__ int s_last;
+    const CompactSeg sg = segs[blockIdx.x];
+    const CompactInst &I = insts[sg.inst];
+    InnerScal *s = I.a.s;
+    if (s->stop) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
+    compact_phase_b<T, NDIM, UN>((const T *)I.a.r, (const T *)I.a.p, (T *)I.a.q, (const T *)I.a.val, I.a.nbr,
+                                 (int)I.a.n, sg.u0 + (int)threadIdx.x, sg.u1, CT, s_pq, s_rq, s_qq, s_rr);
+    T t4[4] = {s_pq, s_rq, s_qq, s_rr};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t4[k] += __shfl_xor_sync(0xffffffffu, t4[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; k++) s_red[warp][k] = t4[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[4] = {0, 0, 0, 0};
+        for (int w = 0; w < CW; w++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) tot[k] += (double)s_red[w][k];
+#pragma unroll
+        for (int k = 0; k < 4; k++) I.part[(long long)sg.slot * 4 + k] = tot[k];
+        __threadfence();
+        const unsigned n = atomicAdd(&s->counter, 1u);
+        s_last = n == (unsigned)I.nseg - 1u;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+        __threadfence();
+        double tot[4] = {0, 0, 0, 0};
+        for (int i = lane; i < I.nseg; i += 32)
+#pragma unroll
+            for (int k = 0; k < 4; k++) tot[k] += __ldcg(I.part + (long long)i * 4 + k);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+        if (lane == 0) {
+            s->counter = 0u;
+            finish_iteration(s, s->iter, tot);
+        }
+    }
+}
 
 template <typename T, int NDIM>
 cudaError_t launch_cg_t(const CompactArgs &a, int grid, cudaStream_t st) {
@@ -470,12 +528,8 @@ cudaError_t launch_cg_t(const CompactArgs &a, int grid, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     CompactArgs arg = a;
-    const long long range = (a.n + grid - 1) / grid;  // the largest CTA range
-    const long long cap = STAGE_BYTES / (long long)sizeof(T);
-    arg.stage_cap = range <= cap ? (int)range : 0;
-    const size_t smem = (size_t)arg.stage_cap * sizeof(T);
     void *params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CT), params, smem,
+    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CTC), params, 0,
                                        st);
 }
 
@@ -484,8 +538,7 @@ int grid_t() {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(compact_cg_kernel<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compact_cg_kernel<T, NDIM>, CT, STAGE_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compact_cg_kernel<T, NDIM>, CTC, 0);
     if (nsm < 1) nsm = 1;
     if (per < 1) per = 1;
     return nsm * per;
@@ -545,11 +598,9 @@ cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f3
 cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st) {
     const long long U = a.n;
     if (f32)
-        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const float *)src, (float *)a.r,
-                                                                (float *)a.r2, a.s);
+        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const float *)src, (float *)a.r);
     else
-        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const double *)src, (double *)a.r,
-                                                                 (double *)a.r2, a.s);
+        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const double *)src, (double *)a.r);
     return cudaGetLastError();
 }
 
@@ -557,10 +608,29 @@ cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, doub
     const long long U = a.n;
     if (f32)
         compact_correct_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, dis, x, (float *)a.y, (const float *)a.p,
-                                                                 (const float *)a.p2, a.s);
+                                                                 a.s);
     else
         compact_correct_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, dis, x, (double *)a.y,
-                                                                  (const double *)a.p, (const double *)a.p2, a.s);
+                                                                  (const double *)a.p, a.s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_batch(int ndim, int f32, const CompactInst *insts, const CompactSeg *segs, int nseg,
+                                 cudaStream_t st) {
+    if (nseg < 1) return cudaSuccess;
+#define NET_CB(T, D)                                                              \
+    do {                                                                          \
+        compact_batch_a_kernel<T, D><<<nseg, CT, 0, st>>>(insts, segs);           \
+        compact_batch_b_kernel<T, D><<<nseg, CT, 0, st>>>(insts, segs);           \
+    } while (0)
+    if (ndim == 2) {
+        if (f32) NET_CB(float, 2);
+        else NET_CB(double, 2);
+    } else {
+        if (f32) NET_CB(float, 3);
+        else NET_CB(double, 3);
+    }
+#undef NET_CB
     return cudaGetLastError();
 }
 

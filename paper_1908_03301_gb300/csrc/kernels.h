@@ -87,10 +87,8 @@ cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st);
 // ---- inner solve over a compacted list of unknowns (cg_compact.cu) --------
 struct CompactArgs {
     long long n;            // unknowns
-    void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each; r, p, q
-    void *r2, *p2, *q2;     //   are double-buffered (set 0, set 1)
+    void *y, *r, *p, *q;    // compact vectors (T), n + 1 entries each
     const int *cidx;        // lattice index of each unknown
-    int stage_cap;          // set at launch: p entries staged in shared memory
     const void *val;        // scaled +e_d bonds [ndim][n + 1] (T; 0: none)
     const int *nbr;         // list indices of the +-e_d neighbours, d = y[, z]:
                             // [2 (ndim - 1)][n]; none: k (+e_d), ~k (-e_d)
@@ -107,12 +105,28 @@ int compact_grid(int ndim, int f32);
 // ELL rows from the scaled lattice bonds gs (T).  cmap: L-entry scratch.
 cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f32, const void *const gs[3],
                           int *cmap, int *cidx, int *nbr, void *val, cudaStream_t st);
-// r[k] = src[cidx[k]] (lattice -> list, T), into the r set the armed inner
-// solve reads first (set (iter + 1) & 1)
+// r[k] = src[cidx[k]] (lattice -> list, T)
 cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st);
 // x[cidx[k]] += D^-1/2 (y[k] (+ alpha p[k] when the pass ended with stop 6))
 cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, double *x, int f32, cudaStream_t st);
 cudaError_t launch_compact_cg(const CompactArgs &a, int ndim, int f32, int grid, cudaStream_t st);
+// Compacted networks inside a batch: every running network's list is cut
+// into segments (one CTA each); one CG iteration of all of them is a launch
+// of phase A then a launch of phase B (the network's last segment reduces
+// the part[] slots in order and runs finish_iteration).
+struct CompactInst {
+    CompactArgs a;   // the network's compact vectors, table and CG state (a.s)
+    double *part;    // 4 partial sums per segment, in slot order
+    int nseg;        // segments of this network in the current plan
+};
+struct CompactSeg {
+    int inst;        // network
+    int u0, u1;      // list range
+    int slot;        // partial-sum slot within the network
+};
+constexpr int COMPACT_SEG = 4096;  // list entries per segment
+cudaError_t launch_compact_batch(int ndim, int f32, const CompactInst *insts, const CompactSeg *segs, int nseg,
+                                 cudaStream_t st);
 
 // ---- persistent sweep over segmented networks (sweep.cu) -------------------
 struct SweepInst;

@@ -222,10 +222,6 @@ NET_API net_status netq_submit(netq_t *q, const net_desc *desc, const void *cons
         set_error("netq_submit: bond planes must be host pointers");
         return NET_EINVAL;
     }
-    if (G.per) {
-        set_error("netq_submit: periodic networks are solved with net_solve");
-        return NET_EINVAL;
-    }
     const int f32 = desc->bond_dtype == NET_F32;
     const size_t foot = net_footprint_bytes(G, f32);
     if (foot > q->budget) {

@@ -141,6 +141,10 @@ size_t net_footprint_bytes(const Geom &g, int raw_f32) {
     b += L * 4;                              // label flags (set-up only)
     b += L * 4;                              // dead-end roots (percolated networks)
     b += L * 4 * (2 * nd + 25);              // set-up only: dead-end loop pass (spanning nodes <= L)
+    // list of unknowns and table when solved on the list: at most 35 % of
+    // the lattice, or all of it for periodic networks (48 B per unknown in
+    // FP32, 76 B in FP64)
+    b += g.per ? L * 80 : L * 20;
     return b;
 }
 
@@ -234,7 +238,7 @@ net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
     CK(dalloc(&cd.cidx, sizeof(int) * (size_t)U, st));
     CK(dalloc(&cd.nbr, sizeof(int) * 2 * (nd - 1) * (size_t)U, st));
     CK(dalloc(&cd.val, es * nd * (size_t)(U + 1), st));
-    CK(dalloc(&cd.vec, es * 7 * (size_t)(U + 1), st));  // y and two sets of r, p, q
+    CK(dalloc(&cd.vec, es * 4 * (size_t)(U + 1), st));
     cd.grid = compact_grid(G.ndim, f32);
     CK(dalloc(&cd.bc, sizeof(InnerScal) * 2, st));
     CK(dalloc(&cd.pb, sizeof(double) * 2 * 4 * (size_t)cd.grid, st));
@@ -280,9 +284,6 @@ CompactArgs compact_args(net_t *n, int f32) {
     a.r = v + 1 * V * es;
     a.p = v + 2 * V * es;
     a.q = v + 3 * V * es;
-    a.r2 = v + 4 * V * es;
-    a.p2 = v + 5 * V * es;
-    a.q2 = v + 6 * V * es;
     a.cidx = cd.cidx;
     a.val = cd.val;
     a.nbr = cd.nbr;
@@ -573,11 +574,13 @@ int prune_level() {
 }
 bool prune_enabled() { return prune_level() > 0; }
 
-// Strip the dead-end trees of the spanning clusters (rounds of removing
-// nodes with at most one link left; see prune_round_kernel), then resolve
-// every removed node to the backbone or face node its tree hangs from.  The
-// removed set is exact at any point: stopping after kMaxRounds only leaves
-// deeper trees in the system.  `pr` is a zeroable L-word scratch buffer.
+// Strip the parts of the spanning clusters that carry no current.  Level 1
+// (NETSOLVE_PRUNE=trees): rounds of removing nodes with at most one link left
+// (see prune_round_kernel), then every removed node resolved to the backbone
+// or face node its tree hangs from; the removed set is exact at any point, so
+// stopping after kMaxRounds only leaves deeper trees in the system.  Level 2
+// (the default): the biconnectivity pass of blocks.cu, which removes trees
+// and dead-end loops alike.  `pr` is a zeroable L-word scratch buffer.
 net_status prune_dead_ends(net_t *n, const void *const gr[3], unsigned int *pr) {
     constexpr unsigned int kChunk = 16, kMaxRounds = 1u << 14;
     cudaStream_t st = n->stream;
@@ -588,7 +591,10 @@ net_status prune_dead_ends(net_t *n, const void *const gr[3], unsigned int *pr) 
     CK(cudaMemsetAsync(n->proot, 0xFF, L * 4, st));  // -1: not removed
     unsigned int round = 0;
     unsigned long long total = 0;
-    while (round < kMaxRounds) {
+    // The biconnectivity pass removes dead-end trees too (no tree node lies on
+    // a path between the faces), in one pass instead of a lattice sweep per
+    // tree generation: the rounds run only when trees alone are stripped.
+    while (prune_level() == 1 && round < kMaxRounds) {
         CK(cudaMemsetAsync(&n->dsc->ss.pruned, 0, sizeof(unsigned int), st));
         for (unsigned int k = 0; k < kChunk; k++)
             CK(launch_prune_round(G, gr, n->raw_f32, n->cls, pr, n->proot, ++round, &n->dsc->ss.pruned, st));
@@ -777,24 +783,33 @@ struct L2Keep {
 // For the compacted solve the correction is applied on the list, and the new
 // scaled residual is gathered from the lattice into the list.
 net_status outer_pass_single(net_t *n, int f32, int apply_corr, const net_opts &o, cudaStream_t st) {
-    if (use_compact_kernel(n, f32)) {
-        net_status s = ensure_compact(n, f32, st);
-        if (s != NET_OK) return s;
-        const CompactDev &cd = n->cp[f32 ? 0 : 1];
-        const CompactArgs ca = compact_args(n, f32);
-        if (apply_corr)
-            CK(launch_compact_correct(ca, n->dis, n->x, f32, st));
-        OuterArgs oa = outer_args(n, f32, 0, f32, o, 1);
-        oa.allow_cont = o.refine != NET_REFINE_RESTART && apply_corr;  // correction applied above
-        CK(launch_outer(oa, st));
-        const InnerArgs ia = inner_args(n, f32);
-        CK(launch_compact_gather(ca, ia.r[0], f32, st));
-        return NET_OK;
-    }
+    if (use_compact_kernel(n, f32)) return outer_pass_compact(n, f32, apply_corr, o, st);
     OuterArgs oa = outer_args(n, f32, apply_corr, f32, o, use_persist_kernel(n, f32));
     CK(launch_outer(oa, st));
     return NET_OK;
 }
+
+// The refinement pass of a network solved on its list of unknowns: the
+// correction applied on the list, the FP64 residual on the lattice, the new
+// scaled residual gathered into the list.
+net_status outer_pass_compact(net_t *n, int f32, int apply_corr, const net_opts &o, cudaStream_t st) {
+    net_status s = ensure_compact(n, f32, st);
+    if (s != NET_OK) return s;
+    const CompactArgs ca = compact_args(n, f32);
+    if (apply_corr) CK(launch_compact_correct(ca, n->dis, n->x, f32, st));
+    OuterArgs oa = outer_args(n, f32, 0, f32, o, 1);
+    oa.allow_cont = o.refine != NET_REFINE_RESTART && apply_corr;  // correction applied above
+    CK(launch_outer(oa, st));
+    const InnerArgs ia = inner_args(n, f32);
+    CK(launch_compact_gather(ca, ia.r[0], f32, st));
+    return NET_OK;
+}
+
+bool batch_takes_compact(const net_t *n, int f32) { return n->g.per != 0 || use_compact_kernel(n, f32); }
+
+net_status prepare_compact(net_t *n, int f32, cudaStream_t st) { return ensure_compact(n, f32, st); }
+
+CompactArgs compact_args_of(net_t *n, int f32) { return compact_args(n, f32); }
 
 // One solve.  Returns the status and fills *r.
 net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {

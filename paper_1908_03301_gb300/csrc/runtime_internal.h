@@ -166,6 +166,15 @@ net_status solve_impl(net_t *n, const net_opts *o, net_result *r);
 net_status arm_for_tuning(net_t *n, int f32, cudaStream_t st);
 // Sweep record of one network for a plan (part / nseg filled by the planner).
 SweepInst sweep_inst_of(net_t *n, int f32);
+// Networks whose unknowns are a small part of the lattice (and periodic
+// ones) are solved on their list of unknowns, in batches too.
+bool batch_takes_compact(const net_t *n, int f32);
+// List of unknowns and table of one inner precision (built on first use).
+net_status prepare_compact(net_t *n, int f32, cudaStream_t st);
+CompactArgs compact_args_of(net_t *n, int f32);
+// Refinement pass of a network solved on its list (correction, FP64
+// residual, gather of the new scaled residual).
+net_status outer_pass_compact(net_t *n, int f32, int apply_corr, const net_opts &o, cudaStream_t st);
 int device_sm_count(int dev);
 // Tune the sweep tile shape over these networks (same dimension, inner
 // precision f32) and store the winner under their key.  Their inner state is

@@ -151,10 +151,11 @@ def fbm_field_aniso(shape, hurst, beta_x, beta_y, gen):
     return field
 
 
-def fbm_aniso_bonds(dims, hurst, beta_x, beta_y, sigma, gen):
-    """Anisotropic correlated conductances g = exp(sigma * B_b), B from Eq. 2."""
+def fbm_aniso_bonds(dims, hurst, beta_x, beta_y, sigma, gen, periodic=()):
+    """Anisotropic correlated conductances g = exp(sigma * B_b), B from Eq. 2
+    (spectral synthesis makes B periodic, so wrap bonds fit it)."""
     B = fbm_field_aniso(node_shape(dims), hurst, beta_x, beta_y, gen)
-    return [np.exp(sigma * b) for b in _node_to_bonds(B, dims)]
+    return [np.exp(sigma * b) for b in _node_to_bonds(B, dims, periodic)]
 
 
 def fbm_bonds(dims, hurst, sigma, gen, periodic=()):
@@ -267,6 +268,20 @@ def aniso_instance(h_index, ratio_index, r, n=512, sigma=1.0):
     gen = rng(SEED_BASE + 1000 * 5 + 100 * (len(ANISO_RATIOS) * h_index + ratio_index) + r)
     dims = (n, n)
     return dims, fbm_aniso_bonds(dims, ANISO_H[h_index], ANISO_RATIOS[ratio_index], 1.0, sigma, gen)
+
+
+def aniso_pair_periodic(h_index, ratio_index, r, n=512, sigma=1.0):
+    """The same realization as aniso_instance with the paper's boundaries
+    (Sec. II: periodic transverse faces), as two networks with the flow along
+    x: the field itself with periodic y (gives K_x), and its transpose with
+    periodic y (the field's x: gives K_y).  Returns [(dims, planes)] * 2."""
+    gen = rng(SEED_BASE + 1000 * 5 + 100 * (len(ANISO_RATIOS) * h_index + ratio_index) + r)
+    dims = (n, n)
+    B = fbm_field_aniso(node_shape(dims), ANISO_H[h_index], ANISO_RATIOS[ratio_index], 1.0, gen)
+    out = []
+    for field in (B, np.ascontiguousarray(B.T)):
+        out.append((dims, [np.exp(sigma * b) for b in _node_to_bonds(field, dims, (1,))]))
+    return out
 
 
 ANISO_H = (0.75, 0.35)

@@ -457,11 +457,11 @@ class Queue:
                "netq_create")
         self.h = h
 
-    def submit(self, dims, planes, flow_axis=0, p_in=1.0, p_out=0.0):
+    def submit(self, dims, planes, flow_axis=0, p_in=1.0, p_out=0.0, periodic=()):
         keep, ptrs, bdt, dev, _ = marshal_planes(planes, len(dims))
         if dev:
             raise TypeError("queue requests take host (numpy) bond planes")
-        desc = make_desc(dims, flow_axis, p_in, p_out, bdt, 0, None)
+        desc = make_desc(dims, flow_axis, p_in, p_out, bdt, 0, None, periodic)
         t = C.c_uint64()
         _check(lib().netq_submit(self.h, C.byref(desc), ptrs, C.byref(t)), "netq_submit")
         return t.value

@@ -50,3 +50,22 @@ def test_kx_equals_ky_of_the_transposed_field(ns):
     with ns.Network(dims, [gx, gy], flow_axis=0) as a, ns.Network(tdims, tplanes, flow_axis=1) as b:
         ra, rb = a.solve(), b.solve()
     assert rel(ra.k_eff, rb.k_eff) <= G_TOL
+
+
+@pytest.mark.parametrize("hi,ri", [(0, 3), (1, 1)])
+def test_periodic_both_axes_batched_match_oracle(ns, hi, ri):
+    """The paper's boundaries (periodic transverse faces): K_x from the field
+    with periodic y, K_y from its transpose with periodic y, all in one batch
+    (the periodic members take the batched compacted path), against the
+    periodic oracle."""
+    pairs = [netgen.aniso_pair_periodic(hi, ri, r, n=64) for r in range(2)]
+    specs = [spec for pair in pairs for spec in pair]
+    nets = [ns.Network(d, p, periodic=(1,)) for d, p in specs]
+    res = ns.solve_batch(nets)
+    for n in nets:
+        n.close()
+    for (d, p), r in zip(specs, res):
+        ref = oracle.solve(d, p, tol=1e-13, periodic=(1,))
+        assert r.status == ns.NET_OK, r
+        assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        assert rel(r.k_eff, ref.k_eff) <= G_TOL

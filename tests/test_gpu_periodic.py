@@ -109,12 +109,46 @@ def test_periodic_wrap_only_path(ns):
     assert rel(r.g_eff, 1.0 / (1.0 / a + 1.0 / w + 1.0 / b)) <= 1e-10
 
 
-def test_periodic_rejected_where_unsupported(ns):
+def test_periodic_networks_in_batch_and_queue(ns):
+    """Periodic members (solved on their list of unknowns, whose table holds
+    the wrap bonds) beside no-flow ones in one batch and in the queue, 2D and
+    3D, dense and percolated: every result against the periodic oracle."""
+    specs = [((48, 40), 0, (1,), 1.0, 40), ((64, 50), 0, (1,), 0.58, 41), ((30, 28, 26), 0, (1, 2), 0.34, 42),
+             ((26, 24, 22), 2, (1,), 0.5, 43), ((40, 36), 1, (), 0.6, 44), ((20, 21, 19), 0, (), 0.4, 45)]
+    nets, refs, inputs = [], [], []
+    for dims, f, per, p, seed in specs:
+        planes = periodic_net(dims, per, p, seed)
+        inputs.append((dims, planes, f, per))
+        refs.append(oracle.solve(dims, planes, flow_axis=f, tol=1e-13, periodic=per))
+        nets.append(ns.Network(dims, planes, flow_axis=f, periodic=per))
+    res = ns.solve_batch(nets)
+    for net, r, ref in zip(nets, res, refs):
+        P = net.pressure()
+        assert r.status == ns.NET_OK, r
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        assert np.max(np.abs(P - ref.P)) <= 1e-7
+    for net in nets:
+        net.close()
+    with ns.Queue(mem_budget_bytes=1 << 30, max_slots=4) as q:
+        tickets = [q.submit(d, pl, flow_axis=f, periodic=per) for d, pl, f, per in inputs]
+        qres = [q.wait(t, timeout_ms=120000) for t in tickets]
+    for (st, r), ref in zip(qres, refs):
+        assert st == ns.NET_OK, (st, r)
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL
+
+
+def test_periodic_rejected_by_autotune(ns):
     dims, per = (16, 12), (1,)
     planes = periodic_net(dims, per, 1.0, 30)
     with ns.Network(dims, planes, periodic=per) as net:
         with pytest.raises(ns.NetError) as e:
-            ns.solve_batch([net])
+            ns.autotune([net])
         assert e.value.status == ns.NET_EINVAL
 
 

@@ -78,3 +78,17 @@ def test_fbm_generator_matches_oracle_filtering():
     gen = netgen.rng(77)
     noise = gen.standard_normal(shape) + 1j * gen.standard_normal(shape)
     np.testing.assert_allclose(field, oracle.fbm_field(noise, 0.7), rtol=0, atol=1e-12)
+
+
+def test_aniso_pair_periodic_is_the_instance_with_wrap_bonds():
+    """The periodic anisotropy pair holds the same realization as the no-flow
+    instance (identical bulk bonds), plus the wrap bonds, and its second
+    network is the transpose of the first."""
+    (d, (gx, gy)), (dt, (tx, ty)) = netgen.aniso_pair_periodic(0, 2, 0, n=32)
+    d0, (ax, ay) = netgen.aniso_instance(0, 2, 0, n=32)
+    assert d == dt == d0 == (32, 32)
+    assert gx.shape == (32, 31) and gy.shape == (32, 32)
+    np.testing.assert_allclose(gx, ax, rtol=0, atol=0)
+    np.testing.assert_allclose(gy[:-1], ay, rtol=0, atol=0)
+    np.testing.assert_allclose(tx, gy[:-1].T, rtol=1e-15)
+    np.testing.assert_allclose(ty[:-1], gx.T, rtol=1e-15)
