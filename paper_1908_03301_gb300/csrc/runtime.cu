@@ -805,7 +805,20 @@ net_status outer_pass_compact(net_t *n, int f32, int apply_corr, const net_opts 
     return NET_OK;
 }
 
-bool batch_takes_compact(const net_t *n, int f32) { return n->g.per != 0 || use_compact_kernel(n, f32); }
+// In a batch the list path's launches are shared by all its members, so it
+// may pay at a higher density than for a network solved alone:
+// NETSOLVE_BATCH_COMPACT_BELOW (a fraction of the lattice) overrides the
+// 35 % of use_compact_kernel for batch members.
+bool batch_takes_compact(const net_t *n, int f32) {
+    if (n->g.per != 0) return true;
+    const char *e = getenv("NETSOLVE_BATCH_COMPACT_BELOW");
+    if (e && *e && n->n_solved > 0) {
+        const double frac = atof(e);
+        const long long lattice = (long long)n->g.nx * n->g.ny * n->g.nz;
+        return (double)n->n_solved < frac * (double)lattice;
+    }
+    return use_compact_kernel(n, f32);
+}
 
 net_status prepare_compact(net_t *n, int f32, cudaStream_t st) { return ensure_compact(n, f32, st); }
 
