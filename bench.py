@@ -168,24 +168,25 @@ def stored_oracle(name):
     return json.load(open(p)).get(name)
 
 
-def oracle_sample(dims, planes, seconds=15.0):
+def oracle_sample(dims, planes, seconds=15.0, nthreads=0):
     """Time the oracle's Jacobi-PCG on the full network for a bounded number of
-    iterations; returns (seconds per iteration, iterations run, threads)."""
+    iterations (nthreads = 0: all cores); returns (seconds per iteration,
+    set-up seconds, iterations run, threads)."""
     import oracle
 
     it = 8
     t = time.perf_counter()
-    oracle.solve(dims, planes, max_iter=1, tol=0.0)  # set-up cost (labels, diagonal)
+    oracle.solve(dims, planes, max_iter=1, tol=0.0, nthreads=nthreads)  # set-up (labels, diagonal)
     t_setup = time.perf_counter() - t
     while True:
         t = time.perf_counter()
-        oracle.solve(dims, planes, max_iter=it, tol=0.0)
+        oracle.solve(dims, planes, max_iter=it, tol=0.0, nthreads=nthreads)
         dt = time.perf_counter() - t
         if dt > seconds / 3 or it >= 4096:
             break
         it *= 2
     per_it = max(dt - t_setup, 1e-9) / (it - 1)
-    return per_it, t_setup, it, oracle.max_threads()
+    return per_it, t_setup, it, (nthreads if nthreads > 0 else oracle.max_threads())
 
 
 # ---------------------------------------------------------------- reference arm
@@ -391,6 +392,12 @@ def run_ours(a, rank, world, local):
             line["cpu_baseline"] = {"value": 1.0 / per_it / 1.0, "unit": "CG iterations/s",
                                     "cores": th, "kind": "oracle",
                                     "sample": f"{it} oracle CG iterations on the full network"}
+        if it_full:
+            # the same on one thread (then every later oracle call names its threads)
+            per1, setup1, it1, _ = oracle_sample(dims, planes, seconds=12.0, nthreads=1)
+            line["cpu_baseline"]["one_thread"] = {
+                "value": 1.0 / (setup1 + per1 * it_full), "unit": "solves/s", "cores": 1,
+                "sample": f"{it1} oracle CG iterations on one thread, scaled to {it_full}"}
         line["cpu_baseline"]["full_solve_64x64"] = oracle_full_small(th)
     print(json.dumps(line), flush=True)
 

@@ -42,6 +42,12 @@
  *
  * Device: the library runs on the CUDA device that is current on the calling
  * thread at net_create / netq_create time and keeps all state resident there.
+ *
+ * Bounded waits: the inner-solve kernels whose CTAs wait for one another at
+ * a grid barrier give up after 2 s of device time (NETSOLVE_WAIT_NS, in
+ * nanoseconds, overrides it); the solve then returns NET_ETIMEOUT and the
+ * device stays usable.  NETSOLVE_WITHHOLD_ARRIVAL=c (testing only) makes CTA
+ * c skip its first arrival so that a test can see the waits run out.
  */
 #ifndef NETSOLVE_H
 #define NETSOLVE_H
@@ -204,7 +210,8 @@ net_status net_create(const net_desc *desc, const void *const g[3], net_t **out)
  * D^-1/2 G D^-1/2.  Pressures stay on the device (net_get_pressure).
  *   opts   NULL = defaults.   out   receives the result (required).
  * Returns out->status: NET_OK, NET_ENOTCONVERGED (caps reached; the result
- * holds the best pressures reached), NET_ECUDA, NET_EINVAL.
+ * holds the best pressures reached), NET_ETIMEOUT (a bounded device wait
+ * gave up; see "Bounded waits" above), NET_ECUDA, NET_EINVAL.
  */
 net_status net_solve(net_t *net, const net_opts *opts, net_result *out);
 
@@ -229,20 +236,27 @@ net_status net_get_pressure(net_t *net, double *dst, int64_t n, int dst_on_devic
 net_status net_get_labels(net_t *net, int32_t *label, uint8_t *cls, int64_t n);
 
 /*
- * Backbone of the spanning clusters: backbone[i] = 1 for the spanning nodes
- * that remain once dead-end trees are stripped, 0 for every other node
- * (host buffer of at least n >= N entries, node layout).
+ * Current-carrying backbone of the spanning clusters: backbone[i] = 1 for the
+ * spanning nodes left in the linear system, 0 for every other node (host
+ * buffer of at least n >= N entries, node layout).
  *
- * A spanning node with at most one open bond to nodes still present (face
- * nodes always count) carries no current: its one bond has no flow, so its
- * pressure equals its neighbour's.  net_create removes such nodes in rounds
- * until none is left (the result is unique); they keep their cluster label
- * and class NET_CLS_SPANNING, but leave the linear system of Eq. 3: the
- * diagonal and the CG sweeps cover the backbone only, and each removed node
- * takes the pressure of the backbone or face node its tree hangs from before
- * every residual pass.  This is exact (the paper solves the whole cluster;
- * it says that near the percolation threshold much of it carries no flow).
- * Set NETSOLVE_PRUNE=0 in the environment to keep the trees in the system.
+ * Take every inlet-face node as one vertex A, every outlet-face node as one
+ * vertex B, and join A and B by one extra edge.  A bond carries current (for
+ * generic conductances) exactly when it lies on a path from A to B that
+ * visits no vertex twice, i.e. when it belongs to the biconnected component
+ * of the extra edge; every other part of a spanning cluster -- a dead-end
+ * tree, or a dead-end loop -- hangs from that component by a single node and
+ * carries no current, so its pressure equals that node's.  net_create finds
+ * the component on the device (Tarjan and Vishkin's parallel biconnectivity
+ * method) and removes the rest: the removed nodes keep their cluster label
+ * and class NET_CLS_SPANNING, but leave the linear system of Eq. 3 (the
+ * diagonal and the CG iterations cover the backbone only), and each takes
+ * the pressure of the node its part hangs from before every residual pass.
+ * This is exact (the paper solves the whole cluster; it says that near the
+ * percolation threshold much of it carries no flow).  The environment
+ * variable NETSOLVE_PRUNE selects less: "trees" removes only the nodes left
+ * with at most one link in rounds (dead-end trees), "0" keeps every spanning
+ * node in the system.
  */
 net_status net_get_backbone(net_t *net, uint8_t *backbone, int64_t n);
 

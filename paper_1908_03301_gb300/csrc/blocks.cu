@@ -2,10 +2,11 @@
 // device (Sec. V and VI.B: near the percolation threshold most of the
 // spanning cluster carries no flow, and solving for it slows CG down).
 //
-// The graph: the nodes left after dead-end trees are stripped ("core" nodes),
-// joined by their open bonds; every inlet-face node taken together as one
-// vertex A and every outlet-face node as one vertex B; and one extra edge
-// A-B.  A bond carries current (for generic conductances) exactly when it lies
+// The graph: the spanning nodes still marked as unknowns ("core" nodes; all
+// spanning nodes, as the round-based tree stripping does not run before this
+// pass by default), joined by their open bonds; every inlet-face node taken
+// together as one vertex A and every outlet-face node as one vertex B; and
+// one extra edge A-B.  A bond carries current (for generic conductances) exactly when it lies
 // on a path from A to B that visits no vertex twice, i.e. when it belongs to
 // the biconnected component (block) of the extra edge.  Every other part of a
 // spanning cluster hangs from that block by one node: a dead-end loop (or a

@@ -245,3 +245,25 @@ def test_near_critical_3d_converges_alone_and_in_batch(ns):
     assert all(r.status == ns.NET_OK for r in res)
     assert res[0].outer_iters <= 20
     assert rel(res[0].g_eff, a.g_eff) <= G_TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_on_lists_matches_oracle(ns, monkeypatch, precision):
+    """Every member of a mixed 2D/3D batch forced onto the batched compacted
+    path (phase launches over list segments, one last-arriver reduction per
+    network), in both precisions: G_eff and pressures against the oracle."""
+    monkeypatch.setenv("NETSOLVE_BATCH_COMPACT_BELOW", "1.01")
+    specs = mixed_nets(10, seed0=500)
+    nets = [ns.Network(d, p) for d, p in specs]
+    res = ns.solve_batch(nets, ns.make_opts(precision=precision))
+    for (dims, planes), net, r in zip(specs, nets, res):
+        assert r.status == ns.NET_OK, r
+        ref = oracle.solve(dims, planes, tol=1e-13)
+        P = net.pressure()
+        if ref.g_eff == 0.0:
+            assert r.g_eff == 0.0
+        else:
+            assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        assert np.max(np.abs(P - ref.P)) <= 1e-7
+    for net in nets:
+        net.close()
