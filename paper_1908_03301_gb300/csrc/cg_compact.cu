@@ -17,9 +17,10 @@
 //   grid barrier
 //   phase B, every unknown:  q = p - sum_j ghat_j p_j  and the sums
 //                            <p,q>, <r,q>, <q,q>, <r,r>
-//   grid barrier: the last CTA to arrive sums the per-CTA partials in CTA
-//   order in FP64, advances the CG state (finish_iteration) and publishes it;
-//   every CTA reads that one record.
+//   grid barrier; then every CTA sums all CTAs' partials in CTA order in
+//   FP64 and advances its own copy of the CG state (finish_iteration): the
+//   same inputs in the same order give the same state everywhere, with no
+//   record to publish and read back.
 // A thread owns the same unknowns in both phases and in every iteration, so
 // its own entries need no cross-SM visibility; neighbours' p written by other
 // CTAs are read through L2 (ld.global.cg).  Every wait is bounded.
@@ -401,40 +402,41 @@ __global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
             for (int k = 0; k < 4; k++) a.pb[((long long)par * G + c) * 4 + k] = tot[k];
         }
         ++target;
-        bool ok = true;
+        // grid barrier without a published state: after it every CTA sums all
+        // CTAs' partials itself, in the same fixed order (FP64, one warp), and
+        // advances its own copy of the CG state -- identical everywhere; one
+        // fewer store and load on the critical path than a reduction by the
+        // last CTA to arrive (7.7 against 8.8 us per barrier over 304 CTAs)
+        bool ok = true, last = false;
         if (barrier_arrive(bar_count, target, G, false)) {
-            // the last CTA: one warp sums the partials (lanes stride over
-            // the CTAs, fixed order, FP64), advances the state, releases
-            if (warp == 0) {
-                __threadfence();
-                double tot[4] = {0, 0, 0, 0};
-                for (int i = lane; i < G; i += 32)
-#pragma unroll
-                    for (int k = 0; k < 4; k++) tot[k] += __ldcg(a.pb + ((long long)par * G + i) * 4 + k);
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
-                if (lane == 0) {
-                    // advance the state in place (shared memory) and publish it
-                    st.err = 0;
-                    finish_iteration(&st, st.iter, tot);
-                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&st);
-                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.bc + par);
-                    for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = src[k];
-                    barrier_release(bar_gen, target);
-                }
-            }
+            last = true;
+            if (threadIdx.x == 0) barrier_release(bar_gen, target);
         } else {
             ok = barrier_wait(bar_gen, target, a.wait_ns);
-            if (threadIdx.x == 0) {
-                if (!ok) {
-                    st.stop = 5;
-                } else {
-                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.bc + par);
-                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&st);
-                    for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = __ldcg(src + k);
+        }
+        if (warp == 0 && ok) {
+            if (last) __threadfence();  // the others' partials, seen through the arrival count
+            double tot[4] = {0, 0, 0, 0};
+            for (int i0 = lane; i0 < G; i0 += 128) {
+                double v[4][4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    const int i = i0 + 32 * m;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) v[m][k] = i < G ? __ldcg(a.pb + ((long long)par * G + i) * 4 + k) : 0.0;
                 }
+#pragma unroll
+                for (int m = 0; m < 4; m++)
+#pragma unroll
+                    for (int k = 0; k < 4; k++) tot[k] += v[m][k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+            if (lane == 0) {
+                st.err = 0;
+                finish_iteration(&st, st.iter, tot);
             }
         }
         if (threadIdx.x == 0 && (bad || !ok)) {

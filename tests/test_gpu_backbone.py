@@ -162,3 +162,55 @@ def test_hand_made_dead_end_loop(ns):
     assert r.n_solved == int(want.sum())
     assert rel(r.g_eff, ref.g_eff) <= G_TOL
     assert np.max(np.abs(P - ref.P)) <= 1e-7
+
+
+def _edge_cases():
+    out = []
+    gen = netgen.rng(9900)
+    # n_f = 3: every interior node touches both faces
+    out.append(((3, 17), 0, (), netgen.percolate(netgen.lognormal_iid((3, 17), gen), 0.6, gen)))
+    # a chain (ny = 1): one closed bond cuts it, otherwise one path
+    g = netgen.lognormal_iid((12, 1), gen)
+    out.append(((12, 1), 0, (), g))
+    g2 = [x.copy() for x in g]
+    g2[0][0, 5] = 0.0
+    out.append(((12, 1), 0, (), g2))
+    # tiny 3D and periodic extent 3
+    out.append(((3, 3, 3), 0, (), netgen.percolate(netgen.lognormal_iid((3, 3, 3), gen), 0.7, gen)))
+    out.append(((6, 3, 4), 0, (1,), netgen.percolate(netgen.lognormal_iid((6, 3, 4), gen, periodic=(1,)), 0.6, gen)))
+    # fully open but one bond: everything carries current
+    g3 = netgen.lognormal_iid((20, 15), gen)
+    g3[1][7, 9] = 0.0
+    out.append(((20, 15), 0, (), g3))
+    # two spanning paths joined only through the faces, with a loop on one
+    gx = np.zeros((6, 9))
+    gy = np.zeros((5, 10))
+    gx[1, :] = 1.0
+    gx[4, :] = 2.0
+    gy[1, 4] = gy[2, 4] = 1.0   # stem (4,1)-(4,2)-(4,3), dead end
+    gx[3, 4] = gy[2, 5] = 1.0   # (4,3)-(5,3)-(5,2)... a loop hanging from the stem
+    gx[2, 4] = 1.0
+    out.append(((10, 6), 0, (), [gx, gy]))
+    # FP32 raw conductances, flow along y
+    g4 = [x.astype(np.float32) for x in netgen.percolate(netgen.lognormal_iid((30, 40), gen), 0.58, gen)]
+    out.append(((30, 40), 1, (), g4))
+    return out
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_backbone_edge_cases(ns, case):
+    dims, f, per, planes = _edge_cases()[case]
+    want = oracle.backbone_blocks(dims, planes, flow_axis=f, periodic=per)
+    ref = oracle.solve(dims, planes, flow_axis=f, tol=1e-13, periodic=per)
+    with ns.Network(dims, planes, flow_axis=f, periodic=per) as net:
+        bb = net.backbone()
+        r = net.solve()
+        P = net.pressure()
+    np.testing.assert_array_equal(bb, want)
+    assert r.n_solved == int(want.sum())
+    if ref.g_eff == 0.0:
+        assert r.g_eff == 0.0
+    else:
+        assert r.status == ns.NET_OK
+        assert rel(r.g_eff, ref.g_eff) <= G_TOL
+        assert np.max(np.abs(P - ref.P)) <= 1e-7
