@@ -554,9 +554,15 @@ def batch_line(a, rank, world, local, n_steps, n_warmup):
     nodes = sum(d[0] * d[1] for d in all_dims)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    split = []  # (set-up seconds, solve seconds) of each step
+
     def one():
+        t0 = time.perf_counter()
         nets = [ns.Network(d, t) for (d, _), t in zip(specs, tpl)]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         res = ns.solve_batch(nets, ns.make_opts(tol_rel=TOL_REL))
+        split.append((t1 - t0, time.perf_counter() - t1))
         for n in nets:
             n.close()
         return res
@@ -588,6 +594,8 @@ def batch_line(a, rank, world, local, n_steps, n_warmup):
         return None
     ui = sum(x[1] for x in allr)
     li = sum(x[4] for x in allr)
+    setup_s = statistics.mean(x[0] for x in split[-len(times):])
+    solve_s = statistics.mean(x[1] for x in split[-len(times):])
     ok = sum(x[0] == 0 for x in allr)
     lat = sorted(x[2] for x in allr)
     peak = measured_hbm_peak()[0]
@@ -606,8 +614,12 @@ def batch_line(a, rank, world, local, n_steps, n_warmup):
             "roofline": {"bound": "hbm", "kernel": "sweep_kernel (all running networks per launch)",
                          "achieved": alg, "peak": peak, "unit": "GB/s", "frac": alg / peak,
                          "lattice_frac": 40 * li / statistics.mean(times) / 1e9 / peak,
-                         "note": "whole-batch wall time including set-up; achieved counts 40 B per "
-                                 "unknown of each linear system per CG iteration"},
+                         "solve_only_frac": 40 * ui / solve_s / 1e9 / peak,
+                         "solve_only_lattice_frac": 40 * li / solve_s / 1e9 / peak,
+                         "note": "achieved / frac: whole-batch wall time including the set-up of "
+                                 "every network; solve_only: net_solve_batch alone; 40 B per unknown "
+                                 "of each linear system (lattice: per lattice node) per CG iteration"},
+            "setup_s": setup_s, "solve_s": solve_s,
             "accuracy": {"max_g_eff_err_estimate": max(x[5] for x in allr)},
             "bytes_note": "algorithmic = 40 B x unknowns in the linear system (dead ends and "
                           "non-spanning clusters excluded) x CG iterations; lattice = 40 B x "

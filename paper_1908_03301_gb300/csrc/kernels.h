@@ -93,7 +93,6 @@ struct CompactArgs {
     const int *nbr;         // list indices of the +-e_d neighbours, d = y[, z]:
                             // [2 (ndim - 1)][n]; none: k (+e_d), ~k (-e_d)
     InnerScal *s;           // armed state in, final state out
-    InnerScal *bc;          // state published by the grid barrier [2]
     double *pb;             // per-CTA partial sums [2][grid][4]
     unsigned *bar;          // grid barrier: arrivals, generation
     int *err;               // set when a bounded wait gave up (cleared at launch)

@@ -240,7 +240,6 @@ net_status ensure_compact(net_t *n, int f32, cudaStream_t st) {
     CK(dalloc(&cd.val, es * nd * (size_t)(U + 1), st));
     CK(dalloc(&cd.vec, es * 4 * (size_t)(U + 1), st));
     cd.grid = compact_grid(G.ndim, f32);
-    CK(dalloc(&cd.bc, sizeof(InnerScal) * 2, st));
     CK(dalloc(&cd.pb, sizeof(double) * 2 * 4 * (size_t)cd.grid, st));
     CK(dalloc(&cd.bar, sizeof(unsigned) * 2, st));
     CK(dalloc(&cd.err, sizeof(int), st));
@@ -288,7 +287,6 @@ CompactArgs compact_args(net_t *n, int f32) {
     a.val = cd.val;
     a.nbr = cd.nbr;
     a.s = &n->dsc->in[k];
-    a.bc = cd.bc;
     a.pb = cd.pb;
     a.bar = cd.bar;
     a.err = cd.err;
@@ -685,7 +683,6 @@ void release_network(net_t *n) {
         dfree(cd.nbr, st);
         dfree(cd.val, st);
         dfree(cd.vec, st);
-        dfree(cd.bc, st);
         dfree(cd.pb, st);
         dfree(cd.bar, st);
         dfree(cd.err, st);

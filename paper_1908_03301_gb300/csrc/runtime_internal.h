@@ -32,7 +32,6 @@ struct CompactDev {
     int *nbr = nullptr;       // [2 (ndim - 1)][U] y/z neighbour list indices
     void *val = nullptr;      // [ndim][U + 1] scaled +e_d bonds
     void *vec = nullptr;      // y, r, p, q, each U + 1 entries
-    InnerScal *bc = nullptr;  // published state [2]
     double *pb = nullptr;     // partial sums [2][grid][4]
     unsigned *bar = nullptr;  // barrier words
     int *err = nullptr;
