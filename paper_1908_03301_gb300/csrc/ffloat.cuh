@@ -1,0 +1,158 @@
+// ffloat.cuh -- float-float ("double-word") scalars for the per-iteration
+// work of the FP32 inner CG loops.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate: one FP64 warp
+// instruction occupies the pipe for about 64 cycles whatever its active
+// lanes, so a one-thread update of the CG scalars in FP64 (two divisions)
+// costs ~2 300 cycles and one thread summing 16 warps' FP32 sums into FP64
+// ~8 700 cycles.  The FP32 inner loops therefore keep their reductions and
+// scalar updates in pairs of FP32 numbers (hi + lo, |lo| <= ulp(hi) / 2):
+// about 48 significant bits, far more than the FP32 vectors the sums come
+// from, at FP32 issue rates (~600 cycles for the update).
+//
+// The building blocks are the classical error-free transformations:
+//   two_sum       Knuth's TwoSum (The Art of Computer Programming, vol. 2,
+//                 sec. 4.2.2): s + e == a + b exactly, any a, b;
+//   fast_two_sum  Dekker's Fast2Sum (Numer. Math. 18, 1971): the same for
+//                 |a| >= |b|;
+//   two_prod      the exact product error through one FMA (as in Ogita, Rump
+//                 and Oishi, SIAM J. Sci. Comput. 26, 2005).
+// Sum, product and quotient of two pairs follow the usual double-word
+// constructions (Joldes, Muller and Popescu, ACM TOMS 44, 2017: the
+// "accurate" sum, a product with the cross terms folded into the error, a
+// quotient refined by one Newton-like correction).  Every operation is an
+// explicitly rounded intrinsic so that no contraction or reassociation can
+// change the results: every CTA that runs the same sequence on the same
+// inputs gets the same bits.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace netsolve {
+
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.h, b.h);
+    const ff t = two_sum(a.l, b.l);
+    s = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(s.h, __fadd_rn(s.l, t.l));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+// Accumulate one FP32 value: the pair stays normalised.
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    const ff s = two_sum(a.h, b);
+    return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const ff r = ff_sub(a, ff_mul({q1, 0.f}, b));
+    const float q2 = __fdiv_rn(r.h, b.h);
+    return fast_two_sum(q1, q2);
+}
+// Exact scaling by 2 (no rounding for normal numbers).
+__device__ __forceinline__ ff ff_twice(ff a) { return {__fmul_rn(2.f, a.h), __fmul_rn(2.f, a.l)}; }
+__device__ __forceinline__ bool ff_le(ff a, ff b) { return a.h < b.h || (a.h == b.h && a.l <= b.l); }
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ ff ff_of(double d) {
+    const float h = __double2float_rn(d);
+    return {h, isfinite(h) ? __double2float_rn(d - (double)h) : 0.f};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return isfinite(a.h) ? (double)a.h + (double)a.l : (double)a.h; }
+
+// The floating fields of InnerScal that one CG iteration reads and writes,
+// as pairs; thr = tol2 * rho0 (fixed while a launch runs).
+struct InnerScalF {
+    ff alpha, beta, rho, best, maxrr, thr, delta2;
+    long long best_iter, iter, max_iter, stag_window;
+    int stop, err, reliable;
+};
+
+__device__ __forceinline__ void scal_to_ff(const InnerScal &s, InnerScalF &f) {
+    f.alpha = ff_of(s.alpha);
+    f.beta = ff_of(s.beta);
+    f.rho = ff_of(s.rho);
+    f.best = ff_of(s.best);
+    f.maxrr = ff_of(s.maxrr);
+    f.thr = ff_of(s.tol2 * s.rho0);
+    f.delta2 = ff_of(s.delta2);
+    f.best_iter = s.best_iter;
+    f.iter = s.iter;
+    f.max_iter = s.max_iter;
+    f.stag_window = s.stag_window;
+    f.stop = s.stop;
+    f.err = s.err;
+    f.reliable = s.reliable;
+}
+__device__ __forceinline__ void scal_from_ff(const InnerScalF &f, InnerScal &s) {
+    s.alpha = ff_to_double(f.alpha);
+    s.beta = ff_to_double(f.beta);
+    s.rho = ff_to_double(f.rho);
+    s.best = ff_to_double(f.best);
+    s.maxrr = ff_to_double(f.maxrr);
+    s.best_iter = f.best_iter;
+    s.iter = f.iter;
+    s.stop = f.stop;
+    s.err = f.err;
+}
+
+// finish_iteration (common.cuh) in float-float: the same tests in the same
+// order on v = {<p,q>, <r,q>, <q,q>, <r,r>} of iteration k.
+__device__ __forceinline__ void finish_iteration_ff(InnerScalF *s, long long k, const ff (&v)[4]) {
+    const ff pq = v[0], rq = v[1], qq = v[2], rr = v[3];
+    s->rho = rr;
+    s->iter = k + 1;
+    if (s->err) {
+        s->stop = 5;
+        return;
+    }
+    if (rr.h == 0.f || (!s->reliable && ff_le(rr, s->thr))) {
+        s->stop = 1;
+        return;
+    }
+    if (!(pq.h > 0.f) || !isfinite(pq.h) || !isfinite(rr.h)) {
+        s->stop = 4;
+        return;
+    }
+    const ff a = ff_div(rr, pq);
+    ff rn1 = ff_add(ff_sub(rr, ff_mul(ff_twice(a), rq)), ff_mul(ff_mul(a, a), qq));
+    if (!(rn1.h > 0.f)) rn1 = {0.f, 0.f};  // cancellation: restart along the residual
+    s->alpha = a;
+    s->beta = ff_div(rn1, rr);
+    if (s->reliable) {
+        if (ff_lt(s->maxrr, rr)) s->maxrr = rr;
+        if (ff_le(rn1, s->thr) || ff_le(rn1, ff_mul(s->delta2, s->maxrr))) {
+            s->stop = 6;
+            return;
+        }
+    }
+    if (ff_lt(rr, {__fmul_rn(0.25f, s->best.h), __fmul_rn(0.25f, s->best.l)})) {
+        s->best = rr;
+        s->best_iter = k;
+    }
+    if (k + 1 >= s->max_iter) s->stop = 2;
+    else if (k - s->best_iter > s->stag_window) s->stop = 3;
+}
+
+}  // namespace netsolve
