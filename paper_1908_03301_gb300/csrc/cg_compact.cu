@@ -44,16 +44,6 @@ constexpr int UNR = 2;                  // unknowns a thread keeps in flight (FP
 constexpr int UNR32 = 2;                // the same in FP32
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // Order of the listed unknowns: whole padded rows (so the +x neighbour of an
 // unknown, if listed, is the next entry), the rows of a 3D network taken in
@@ -208,37 +198,18 @@ __global__ void compact_correct_kernel(long long U, const int *__restrict__ cidx
 }
 
 // ------------------------------------------------------------------ the solve
-// Grid barrier: every CTA's writes are done, thread 0 adds its arrival to the
-// count (red.release, no value returned) and polls the count until all G
-// CTAs of barrier `n` have arrived (count == G n, compared modulo 2^32: the
-// count is never more than G arrivals away from the goal).  No CTA releases
-// the others, which saves the last arriver's atomic round trip and release
-// store (2.08 against 2.96 us per barrier over 304 CTAs in a stand-alone
-// probe).  Returns to all threads whether the wait ended before wait_ns of
-// device time.  `withhold`: for tests of the bounded wait, this CTA does not
+// Grid barrier (arrive_release / wait_count): every CTA's writes are done,
+// thread 0 arrives and waits; returns to all threads whether the wait ended
+// in time.  `withhold`: for tests of the bounded wait, this CTA does not
 // arrive.
-__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned goal, unsigned long long wait_ns,
                                              bool withhold) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (!withhold) red_release_add_u32(count, 1u);
-        // poll with relaxed loads (an acquire per poll would order, and slow,
-        // the memory traffic of the other CTA on this SM), then one acquire
-        bool ok = false;
-        const unsigned long long t0 = globaltimer_ns();
-        for (uint32_t i = 0;; i++) {
-            if ((int)(ld_relaxed_u32(count) - goal) >= 0) {
-                ok = (int)(ld_acquire_u32(count) - goal) >= 0;
-                break;
-            }
-            if ((i & 255u) == 255u && globaltimer_ns() - t0 > wait_ns) break;
-        }
-        s_ok = ok;
+        if (!withhold) arrive_release(count);
+        s_ok = wait_count(count, goal, wait_ns);
     }
     __syncthreads();
     return s_ok != 0;
@@ -354,36 +325,8 @@ __device__ __forceinline__ void cta_sums(const double (*s_red)[4], double (&t)[4
 #pragma unroll
         for (int k = 0; k < 4; k++) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
 }
-// All G CTAs' partials of one parity, summed by one warp: lane-strided, four
-// CTAs per lane in flight, then a butterfly.  The same inputs in the same
-// order give the same bits in every CTA.  FP32: partial i is the float4 pair
-// {hi[4], lo[4]} at part[2 i], part[2 i + 1].
-__device__ __forceinline__ void grid_sums(const float4 *part, int G, ff (&tot)[4]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < 4; k++) tot[k] = {0.f, 0.f};
-    for (int i0 = lane; i0 < G; i0 += 128) {
-        float4 h[4], l[4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            const int i = i0 + 32 * m;
-            h[m] = i < G ? __ldcg(part + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            l[m] = i < G ? __ldcg(part + 2 * i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            tot[0] = ff_add(tot[0], {h[m].x, l[m].x});
-            tot[1] = ff_add(tot[1], {h[m].y, l[m].y});
-            tot[2] = ff_add(tot[2], {h[m].z, l[m].z});
-            tot[3] = ff_add(tot[3], {h[m].w, l[m].w});
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            tot[k] = ff_add(tot[k], {__shfl_xor_sync(0xffffffffu, tot[k].h, o), __shfl_xor_sync(0xffffffffu, tot[k].l, o)});
-}
+// All G CTAs' FP64 partials of one parity, summed by one warp as
+// warp_sum_pairs (ffloat.cuh) sums the FP32 solve's pairs.
 __device__ __forceinline__ void grid_sums(const double *part, int G, double (&tot)[4]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -513,7 +456,7 @@ __global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
         if (warp == 0 && ok) {
             S tot[4];
             if constexpr (sizeof(T) == 4)
-                grid_sums(reinterpret_cast<const float4 *>(a.pb) + 2LL * par * G, G, tot);
+                warp_sum_pairs(reinterpret_cast<const float4 *>(a.pb) + 2LL * par * G, G, tot);
             else
                 grid_sums(a.pb + 4LL * par * G, G, tot);
             if (lane == 0) sc.finish(tot);

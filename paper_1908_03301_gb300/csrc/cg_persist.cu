@@ -16,14 +16,18 @@
 //    pipeline and starts the next sweep's rows before the grid barrier;
 //    16 consumer warps own column strips and keep the march neighbours in
 //    registers, meeting only at the pipeline's mbarriers;
-//  * one grid barrier per sweep; afterwards every CTA sums all CTAs' partials
-//    in CTA order (deterministic, identical everywhere) and advances the same
-//    CG state held in shared memory.  CTA 0 writes the final state back.
+//  * one grid barrier per sweep (arrivals counted, every CTA polls the
+//    count); afterwards every CTA sums all CTAs' partials in the same fixed
+//    order and advances its own copy of the CG state -- identical everywhere.
+//    The sums and the state are float-float pairs (ffloat.cuh): GB300's FP64
+//    rate would put microseconds of FP64 on every sweep's critical path.
+//    CTA 0 writes the final state back.
 // Every wait is bounded; a wait that gives up poisons the sums (the solve
 // stops as a breakdown) and sets *err.
 #include <cfloat>
 #include <cmath>
 
+#include "ffloat.cuh"
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -56,19 +60,6 @@ __device__ __forceinline__ float *hrow(unsigned char *smem, int e, int a) {
     return reinterpret_cast<float *>(smem + BAR + HALO + (e * 3 + a) * ROWB);
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ __forceinline__ float rnew(float r, float q, float a) { return fmaf(-a, q, r); }
 __device__ __forceinline__ float pnew(float rn, float p, float b) { return fmaf(b, p, rn); }
@@ -127,8 +118,9 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
     uint64_t *empty = full + S;
     uint64_t *hfull = empty + S;  // halo rows of the current sweep
     __shared__ InnerScal st;
+    __shared__ InnerScalF sf;  // the running state, as pairs
     __shared__ float s_red[NCW][4];
-    __shared__ int s_bad, s_last;
+    __shared__ int s_bad;
 
     const int G = gridDim.x, c = blockIdx.x;
     const int px = a.g.px, ny = a.g.ny;
@@ -147,6 +139,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
         mbar_init(hfull, 1);
         mbar_fence_init();
         st = *a.s;
+        scal_to_ff(st, sf);
         s_bad = 0;
     }
     __syncthreads();
@@ -180,10 +173,12 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             for (; pre < S && pre < steps; pre++) producer_issue(pre - 1, first);
     }
 
-    for (int sweep = 0;; sweep++) {
-        if (st.stop) break;
-        const bool first = st.iter == 0;
-        const float alpha = (float)st.alpha, beta = (float)st.beta;
+    unsigned goal = 0;  // arrivals the next grid barrier waits for
+    int sweep = 0;
+    for (;; sweep++) {
+        if (sf.stop) break;
+        const bool first = sf.iter == 0;
+        const float alpha = sf.alpha.h, beta = sf.beta.h;
         const int par = sweep & 1, ppar = par ^ 1;
 
         if (warp == NCW) {
@@ -367,8 +362,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                 h0r = h1r;
                 r_cur = r_next;
             }
-            // this CTA's sums, in FP32 like the rest of the inner loop (GB300
-            // runs FP64 far slower; only the cross-CTA sum below is FP64)
+            // this CTA's sums: FP32 within each warp, then a float-float pair
             float v4[4] = {a_pq, a_rq, a_qq, a_rr};
 #pragma unroll
             for (int k = 0; k < 4; k++)
@@ -379,84 +373,45 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
                 for (int k = 0; k < 4; k++) s_red[warp][k] = v4[k];
             asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
             if (threadIdx.x == 0) {
-                float tot[4] = {0.f, 0.f, 0.f, 0.f};
+                ff tot[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 for (int wi = 0; wi < NCW; wi++)
 #pragma unroll
-                    for (int k = 0; k < 4; k++) tot[k] += s_red[wi][k];
-                if (s_bad) tot[3] = NAN;
-                *reinterpret_cast<float4 *>(a.pb + ((long long)par * G + c) * 4) =
-                    make_float4(tot[0], tot[1], tot[2], tot[3]);
+                    for (int k = 0; k < 4; k++) tot[k] = ff_add_f(tot[k], s_red[wi][k]);
+                if (s_bad) tot[3] = {NAN, 0.f};
+                float4 *dst = reinterpret_cast<float4 *>(a.pb) + 2 * ((long long)par * G + c);
+                dst[0] = make_float4(tot[0].h, tot[1].h, tot[2].h, tot[3].h);
+                dst[1] = make_float4(tot[0].l, tot[1].l, tot[2].l, tot[3].l);
             }
         }
         __syncthreads();  // A: this CTA's rows, halo copies and sums are written
-        const unsigned target = (unsigned)sweep + 1u;
+        goal += (unsigned)G;
         if (warp == NCW) {
             // start the next sweep's own rows (written by this CTA itself);
             // if the solve stops instead, they are drained below
             asm volatile("fence.proxy.async.global;" ::: "memory");
             for (; pre < S && pre < steps; pre++) producer_issue(pre - 1, false);
-        } else if (threadIdx.x == 0) {
-            // grid barrier, part 1: arrive (a CTA told to withhold its
-            // first arrival, for tests of the bounded wait, does not)
-            __threadfence();
-            if (sweep == 0 && c == a.skip_cta) {
-                s_last = 0;
-            } else {
-                const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
-                s_last = arrived == (unsigned)G * target;
-            }
-            if (s_bad) atomicExch(a.err, 1);
-        }
-        __syncthreads();  // B
-        if (s_last) {
-            // the last CTA to arrive: sum all partials in CTA order (FP64, one
-            // warp), advance the CG state and publish it with the release
-            if (warp == 0) {
+        } else if (warp == 0) {
+            // grid barrier (a CTA told to withhold its first arrival, for
+            // tests of the bounded wait, does not arrive), then this CTA's own
+            // sum of all partials and its own step of the CG state
+            int ok = 0;
+            if (lane == 0) {
                 __threadfence();
-                double tot[4] = {0, 0, 0, 0};
-                for (int i = lane; i < G; i += 32) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(a.pb + ((long long)par * G + i) * 4));
-                    tot[0] += v.x;
-                    tot[1] += v.y;
-                    tot[2] += v.z;
-                    tot[3] += v.w;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+                if (!(sweep == 0 && c == a.skip_cta)) arrive_release(a.bar_count);
+                if (s_bad) atomicExch(a.err, 1);
+                ok = wait_count(a.bar_count, goal, a.wait_ns);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok) {
+                ff tot[4];
+                warp_sum_pairs(reinterpret_cast<const float4 *>(a.pb) + 2LL * par * G, G, tot);
                 if (lane == 0) {
-                    st.err = 0;
-                    finish_iteration(&st, st.iter, tot);
-                    a.bc[par] = st;
-                    __threadfence();
-                    st_release(a.bar_gen, target);
+                    sf.err = 0;
+                    finish_iteration_ff(&sf, sf.iter, tot);
                 }
-            }
-        } else if (threadIdx.x == 0) {
-            // grid barrier, part 2: wait for the release, read the new state
-            // relaxed polls, then one acquire: an acquire per poll would
-            // order (and slow) this SM's other memory traffic
-            // (gives up after a.wait_ns of device time)
-            bool ok = false;
-            const unsigned long long t0 = globaltimer_ns();
-            for (uint32_t i = 0;; i++) {
-                if (ld_relaxed(a.bar_gen) >= target) {
-                    ok = ld_acquire(a.bar_gen) >= target;
-                    break;
-                }
-                if ((i & 255u) == 255u && globaltimer_ns() - t0 > a.wait_ns) break;
-            }
-            if (!ok) {
+            } else if (lane == 0) {
                 atomicExch(a.err, 1);
-                st.stop = 5;
-            } else {
-                const InnerScal *bc = a.bc + par;
-                InnerScal ns;
-                const unsigned long long *src = reinterpret_cast<const unsigned long long *>(bc);
-                unsigned long long *dst = reinterpret_cast<unsigned long long *>(&ns);
-                for (int k = 0; k < (int)(sizeof(InnerScal) / 8); k++) dst[k] = __ldcg(src + k);
-                st = ns;
+                sf.stop = 5;
             }
         }
         __syncthreads();  // C
@@ -468,6 +423,7 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
     }
     if (c == 0 && threadIdx.x == 0) {
         InnerScal out = st;
+        if (sweep > 0) scal_from_ff(sf, out);  // untouched when no sweep ran
         out.counter = 0u;
         *a.s = out;
     }
@@ -529,7 +485,7 @@ cudaError_t launch_persist(const PersistArgs &a, int grid, cudaStream_t st) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persist_kernel, NTH, SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    e = cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned) * 2, st);  // arrivals and generation
+    e = cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned), st);  // arrivals
     if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     PersistArgs arg = a;

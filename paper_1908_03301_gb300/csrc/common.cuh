@@ -237,6 +237,34 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// Grid barrier of the cooperative kernels, one counter for the whole launch
+// (zeroed before it): each CTA, its writes done, adds its arrival with
+// release semantics and no value returned; barrier n is passed when the count
+// reaches G n.  Every CTA polls the count itself: nobody has to arrive last
+// and release the others, which saves an atomic round trip and a release
+// store per barrier (2.08 against 2.96 us over 304 CTAs in a stand-alone
+// probe).
+__device__ __forceinline__ void arrive_release(unsigned *count) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+}
+// Waits until *count has reached goal (compared modulo 2^32: the count is
+// never more than G arrivals away from a goal being waited for).  Relaxed
+// polls -- an acquire per poll would order, and slow, the memory traffic of
+// the other CTA on the SM -- then one acquire.  Gives up, returning false,
+// after wait_ns of device time.
+__device__ __forceinline__ bool wait_count(const unsigned *count, unsigned goal, unsigned long long wait_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned i = 0;; i++) {
+        unsigned v;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if ((int)(v - goal) >= 0) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            return (int)(v - goal) >= 0;
+        }
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > wait_ns) return false;
+    }
+}
+
 // 16-byte vector of T (float4 / double2) with element access.
 template <typename T> struct Vec;
 template <> struct Vec<float> {

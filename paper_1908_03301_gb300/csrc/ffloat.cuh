@@ -81,6 +81,37 @@ __device__ __forceinline__ ff ff_of(double d) {
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return isfinite(a.h) ? (double)a.h + (double)a.l : (double)a.h; }
 
+// Sum of G per-CTA pairs of four sums by one warp: pair i is the float4s
+// {hi[4]} at part[2 i] and {lo[4]} at part[2 i + 1].  Lane-strided, four
+// CTAs per lane in flight, then a butterfly; the same inputs give the same
+// bits in every lane and every CTA.
+__device__ __forceinline__ void warp_sum_pairs(const float4 *part, int G, ff (&tot)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) tot[k] = {0.f, 0.f};
+    for (int i0 = lane; i0 < G; i0 += 128) {
+        float4 h[4], l[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const int i = i0 + 32 * m;
+            h[m] = i < G ? __ldcg(part + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            l[m] = i < G ? __ldcg(part + 2 * i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            tot[0] = ff_add(tot[0], {h[m].x, l[m].x});
+            tot[1] = ff_add(tot[1], {h[m].y, l[m].y});
+            tot[2] = ff_add(tot[2], {h[m].z, l[m].z});
+            tot[3] = ff_add(tot[3], {h[m].w, l[m].w});
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            tot[k] = ff_add(tot[k], {__shfl_xor_sync(0xffffffffu, tot[k].h, o), __shfl_xor_sync(0xffffffffu, tot[k].l, o)});
+}
+
 // The floating fields of InnerScal that one CG iteration reads and writes,
 // as pairs; thr = tol2 * rho0 (fixed while a launch runs).
 struct InnerScalF {

@@ -71,10 +71,8 @@ struct PersistArgs {
     float *y, *r, *p, *q;      // inner vectors, updated in place
     InnerScal *s;              // armed state in, final state out
     float *hb;                 // halo copies [2][grid][2][3][px]
-    float *pb;                 // per-CTA sums [2][grid][4]
-    InnerScal *bc;             // state published by the barrier [2]
-    unsigned *bar_count;       // grid barrier: arrivals (bar_count[0]) and
-    unsigned *bar_gen;         //   generation (bar_gen == bar_count + 1)
+    float *pb;                 // per-CTA sums as pairs [2][grid][hi 4, lo 4]
+    unsigned *bar_count;       // grid barrier: arrivals (zeroed at launch)
     int *err;                  // set when a bounded wait gave up (cleared at launch)
     unsigned long long wait_ns;  // give up a grid-barrier wait after this long
     int skip_cta;              // testing: this CTA withholds its first arrival (-1: none)

@@ -301,8 +301,7 @@ net_status ensure_persist(net_t *n) {
     const int grid = persist_grid(n->g);
     // halo copies: [sweep parity][CTA][first/last row][r, q, p][px]
     CK(dalloc(&n->ps_hb, sizeof(float) * 2 * 2 * 3 * (size_t)grid * n->g.px, st));
-    CK(dalloc(&n->ps_pb, sizeof(float) * 2 * 4 * (size_t)grid, st));
-    CK(dalloc(&n->ps_bc, sizeof(InnerScal) * 2, st));
+    CK(dalloc(&n->ps_pb, sizeof(float) * 2 * 8 * (size_t)grid, st));
     CK(dalloc(&n->ps_bar, sizeof(unsigned) * 2, st));
     CK(dalloc(&n->ps_err, sizeof(int), st));
     CK(persist_prepare());
@@ -697,7 +696,6 @@ void release_network(net_t *n) {
     for (int d = 0; d < 3; d++) dfree(n->graw[d], st);
     dfree(n->ps_hb, st);
     dfree(n->ps_pb, st);
-    dfree(n->ps_bc, st);
     dfree(n->ps_bar, st);
     dfree(n->ps_err, st);
     dfree(n->parent, st);
@@ -921,9 +919,7 @@ net_status solve_impl(net_t *n, const net_opts *o_in, net_result *r) {
             pa.s = ds;
             pa.hb = n->ps_hb;
             pa.pb = n->ps_pb;
-            pa.bc = n->ps_bc;
             pa.bar_count = n->ps_bar;
-            pa.bar_gen = n->ps_bar + 1;
             pa.err = n->ps_err;
             pa.wait_ns = grid_wait_ns();
             pa.skip_cta = withheld_arrival_cta();

@@ -75,7 +75,6 @@ struct net_s {
     // barrier words, error word
     float *ps_hb = nullptr;
     float *ps_pb = nullptr;
-    netsolve::InnerScal *ps_bc = nullptr;
     unsigned *ps_bar = nullptr;
     int *ps_err = nullptr;
     int ps_grid = 0;
