@@ -132,7 +132,7 @@ def kernel_source_hash():
     """Hash of the persistent kernel's code (its source and headers with
     // comments and blank lines left out: the counters depend on the code)."""
     h = hashlib.sha256()
-    for name in ("cg_persist.cu", "common.cuh", "tma.cuh"):
+    for name in ("cg_persist.cu", "common.cuh", "ffloat.cuh", "tma.cuh"):
         for line in open(os.path.join(ROOT, "paper_1908_03301_gb300", "csrc", name), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
             if code:

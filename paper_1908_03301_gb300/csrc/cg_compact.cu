@@ -17,10 +17,12 @@
 //   grid barrier
 //   phase B, every unknown:  q = p - sum_j ghat_j p_j  and the sums
 //                            <p,q>, <r,q>, <q,q>, <r,r>
-//   grid barrier; then every CTA sums all CTAs' partials in CTA order in
-//   FP64 and advances its own copy of the CG state (finish_iteration): the
-//   same inputs in the same order give the same state everywhere, with no
-//   record to publish and read back.
+//   grid barrier; then every CTA sums all CTAs' partials in the same fixed
+//   order and advances its own copy of the CG state: the same inputs in the
+//   same order give the same state everywhere, with no record to publish and
+//   read back.  The FP32 solve keeps its sums and scalars as float-float
+//   pairs (ffloat.cuh; GB300's FP64 rate would put microseconds of FP64 on
+//   every iteration), the FP64 solve in FP64.
 // A thread owns the same unknowns in both phases and in every iteration, so
 // its own entries need no cross-SM visibility; neighbours' p written by other
 // CTAs are read through L2 (ld.global.cg).  Every wait is bounded.
@@ -303,28 +305,6 @@ __device__ __forceinline__ void compact_phase_b(const T *__restrict__ r, const T
     }
 }
 
-// The four sums of one CTA (s_red: one row per warp), combined by warp 0 in a
-// fixed tree over the 16 rows.  FP32 sums become a float-float pair; FP64
-// ones stay FP64.  Every lane ends with the same result.
-__device__ __forceinline__ void cta_sums(const float (*s_red)[4], ff (&t)[4]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < 4; k++) t[k] = {s_red[lane & (CWC - 1)][k], 0.f};
-#pragma unroll
-    for (int o = CWC / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            t[k] = ff_add(t[k], {__shfl_xor_sync(0xffffffffu, t[k].h, o), __shfl_xor_sync(0xffffffffu, t[k].l, o)});
-}
-__device__ __forceinline__ void cta_sums(const double (*s_red)[4], double (&t)[4]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < 4; k++) t[k] = s_red[lane & (CWC - 1)][k];
-#pragma unroll
-    for (int o = CWC / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 4; k++) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
-}
 // All G CTAs' FP64 partials of one parity, summed by one warp as
 // warp_sum_pairs (ffloat.cuh) sums the FP32 solve's pairs.
 __device__ __forceinline__ void grid_sums(const double *part, int G, double (&tot)[4]) {
@@ -433,7 +413,7 @@ __global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
         const int par = (int)(sc.iter() & 1);
         if (warp == 0) {
             S t[4];
-            cta_sums(s_red, t);
+            warp_sum_rows<CWC>(s_red, t);
             if (lane == 0) {
                 if constexpr (sizeof(T) == 4) {
                     float4 *dst = reinterpret_cast<float4 *>(a.pb) + 2 * ((long long)par * G + c);
@@ -481,8 +461,8 @@ __global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
 // iteration for every running network of the group (the kernel boundary is
 // the barrier between the phases), a network cut into segments of list
 // entries, one segment per CTA.  A network's last segment to finish phase B
-// sums the segments' partials in slot order (FP64) and runs finish_iteration,
-// as the lattice sweep does; stopped networks are skipped.
+// sums the segments' partials (pairs in the FP32 path) in slot order and runs
+// finish_iteration, as the lattice sweep does; stopped networks are skipped.
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(CT) compact_batch_a_kernel(const CompactInst *__restrict__ insts,
                                                              const CompactSeg *__restrict__ segs) {
@@ -518,28 +498,21 @@ __global__ void __launch_bounds__(CT) compact_batch_b_kernel(const CompactInst *
 #pragma unroll
         for (int k = 0; k < 4; k++) s_red[warp][k] = t4[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot[4] = {0, 0, 0, 0};
-        for (int w = 0; w < CW; w++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) tot[k] += (double)s_red[w][k];
-#pragma unroll
-        for (int k = 0; k < 4; k++) I.part[(long long)sg.slot * 4 + k] = tot[k];
-        __threadfence();
-        const unsigned n = atomicAdd(&s->counter, 1u);
-        s_last = n == (unsigned)I.nseg - 1u;
+    if (warp == 0) {
+        typename std::conditional<sizeof(T) == 4, ff, double>::type t[4];
+        warp_sum_rows<CW>(s_red, t);
+        if (lane == 0) {
+            store_slot(I.part, sg.slot, t, false);
+            __threadfence();
+            const unsigned n = atomicAdd(&s->counter, 1u);
+            s_last = n == (unsigned)I.nseg - 1u;
+        }
     }
     __syncthreads();
     if (s_last && warp == 0) {
         __threadfence();
-        double tot[4] = {0, 0, 0, 0};
-        for (int i = lane; i < I.nseg; i += 32)
-#pragma unroll
-            for (int k = 0; k < 4; k++) tot[k] += __ldcg(I.part + (long long)i * 4 + k);
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+        double tot[4];
+        sum_slots(I.part, I.nseg, tot, T(0));
         if (lane == 0) {
             s->counter = 0u;
             finish_iteration(s, s->iter, tot);

@@ -112,6 +112,64 @@ __device__ __forceinline__ void warp_sum_pairs(const float4 *part, int G, ff (&t
             tot[k] = ff_add(tot[k], {__shfl_xor_sync(0xffffffffu, tot[k].h, o), __shfl_xor_sync(0xffffffffu, tot[k].l, o)});
 }
 
+// The four sums of NR rows (one row per warp of a CTA), combined by one warp
+// in a fixed tree: FP32 rows into pairs, FP64 rows in FP64.  NR is a power of
+// two <= 32; every lane ends with the same result.
+template <int NR>
+__device__ __forceinline__ void warp_sum_rows(const float (*rows)[4], ff (&t)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) t[k] = {rows[lane & (NR - 1)][k], 0.f};
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            t[k] = ff_add(t[k], {__shfl_xor_sync(0xffffffffu, t[k].h, o), __shfl_xor_sync(0xffffffffu, t[k].l, o)});
+}
+template <int NR>
+__device__ __forceinline__ void warp_sum_rows(const double (*rows)[4], double (&t)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) t[k] = rows[lane & (NR - 1)][k];
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; k++) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+}
+
+// Per-segment slots of the batched kernels: 32 bytes each, four FP64 sums or
+// (FP32 path) one pair {hi[4]}, {lo[4]} of float4s.  `zero`: store zeros.
+__device__ __forceinline__ void store_slot(double *part, long long slot, const ff (&t)[4], bool zero) {
+    float4 *d = reinterpret_cast<float4 *>(part) + 2 * slot;
+    d[0] = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(t[0].h, t[1].h, t[2].h, t[3].h);
+    d[1] = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(t[0].l, t[1].l, t[2].l, t[3].l);
+}
+__device__ __forceinline__ void store_slot(double *part, long long slot, const double (&t)[4], bool zero) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) part[slot * 4 + k] = zero ? 0.0 : t[k];
+}
+// A network's total over its nseg slots, by one warp, as FP64 for
+// finish_iteration (the FP32 path sums the pairs and converts the four
+// totals once).
+__device__ __forceinline__ void sum_slots(const double *part, int nseg, double (&tot)[4], float /*FP32 path*/) {
+    ff t[4];
+    warp_sum_pairs(reinterpret_cast<const float4 *>(part), nseg, t);
+#pragma unroll
+    for (int k = 0; k < 4; k++) tot[k] = ff_to_double(t[k]);
+}
+__device__ __forceinline__ void sum_slots(const double *part, int nseg, double (&tot)[4], double /*FP64 path*/) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) tot[k] = 0.0;
+    for (int i = lane; i < nseg; i += 32)
+#pragma unroll
+        for (int k = 0; k < 4; k++) tot[k] += __ldcg(part + (long long)i * 4 + k);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+}
+
 // The floating fields of InnerScal that one CG iteration reads and writes,
 // as pairs; thr = tol2 * rho0 (fixed while a launch runs).
 struct InnerScalF {

@@ -28,7 +28,9 @@
 // CTA keeps the barrier protocol so that every issued copy is waited for.
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
+#include "ffloat.cuh"
 #include "kernels.h"
 #include "sweep.cuh"
 #include "tma.cuh"
@@ -335,7 +337,7 @@ __device__ SegView seg_view(const SweepSeg &sg, const SweepInst &I) {
 template <typename T>
 __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t *empty,
                                    const SweepInst &I, const SweepSeg &sg, long long &G,
-                                   uint32_t &lim, int *s_err, double (&acc)[4]) {
+                                   uint32_t &lim, int *s_err, T (&acc)[4]) {
     using C = SW<T, 2>;
     constexpr int V = C::V, VT = C::VT, S = C::S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -469,10 +471,10 @@ __device__ void consume_segment_2d(unsigned char *smem, uint64_t *full, uint64_t
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[b])) : "memory");
     }
-    acc[0] = (double)a_pq;
-    acc[1] = (double)a_rq;
-    acc[2] = (double)a_qq;
-    acc[3] = (double)a_rr;
+    acc[0] = a_pq;
+    acc[1] = a_rq;
+    acc[2] = a_qq;
+    acc[3] = a_rr;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -485,7 +487,7 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + S;
-    __shared__ double s_red[NCW][4];
+    __shared__ T s_red[NCW][4];
     __shared__ int s_last, s_err;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -558,7 +560,7 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
         const SweepSeg sg = segs[si];
         const SweepInst &I = insts[sg.inst];
         if (inst_stopped(I)) continue;
-        double v4[4];
+        T v4[4];
         if constexpr (NDIM == 2) {
             consume_segment_2d<T>(smem, full, empty, I, sg, G, lim, &s_err, v4);
         } else {
@@ -760,50 +762,40 @@ sweep_kernel(const SweepInst *__restrict__ insts, const SweepSeg *__restrict__ s
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[b])) : "memory");
         }
 
-        v4[0] = (double)a_pq;
-        v4[1] = (double)a_rq;
-        v4[2] = (double)a_qq;
-        v4[3] = (double)a_rr;
+        v4[0] = a_pq;
+        v4[1] = a_rq;
+        v4[2] = a_qq;
+        v4[3] = a_rr;
         }
         // ---- segment sums -> the network's slot; last arrival finishes ----
-        // CTA-level sums in T (FP32 for the mixed path: GB300's FP64 rate
-        // makes a 16-warp FP64 reduction cost microseconds); the final sum
-        // over the network's segments is FP64, in one warp.
-        T t4[4] = {(T)v4[0], (T)v4[1], (T)v4[2], (T)v4[3]};
+        // Sums stay in T up to the warp; warp 0 combines the warps in a fixed
+        // tree (FP32 path: into a float-float pair) -- GB300's FP64 rate makes
+        // every FP64 instruction here cost ~64 cycles -- and the network's
+        // last segment sums the slots in one warp.
 #pragma unroll
         for (int k = 0; k < 4; k++)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t4[k] += __shfl_xor_sync(0xffffffffu, t4[k], off);
+            for (int off = 16; off > 0; off >>= 1) v4[k] += __shfl_xor_sync(0xffffffffu, v4[k], off);
         if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < 4; k++) s_red[warp][k] = (double)t4[k];
+            for (int k = 0; k < 4; k++) s_red[warp][k] = v4[k];
         cons_sync();
-        if (c == 0) {
-            T tot[4] = {T(0), T(0), T(0), T(0)};
-            for (int wi = 0; wi < NCW; wi++)
-#pragma unroll
-                for (int k = 0; k < 4; k++) tot[k] += (T)s_red[wi][k];
-            if (s_err) {
-                atomicExch(&I.s->err, 1);
-                tot[0] = tot[1] = tot[2] = tot[3] = T(0);
+        if (warp == 0) {
+            typename std::conditional<sizeof(T) == 4, ff, double>::type t[4];
+            warp_sum_rows<NCW>(s_red, t);
+            if (lane == 0) {
+                if (s_err) atomicExch(&I.s->err, 1);
+                store_slot(I.part, sg.slot, t, s_err != 0);
+                __threadfence();
+                const unsigned int n = atomicAdd(&I.s->counter, 1u);
+                s_last = (n == (unsigned)I.nseg - 1);
             }
-#pragma unroll
-            for (int k = 0; k < 4; k++) I.part[sg.slot * 4 + k] = (double)tot[k];
-            __threadfence();
-            const unsigned int n = atomicAdd(&I.s->counter, 1u);
-            s_last = (n == (unsigned)I.nseg - 1);
         }
         cons_sync();
         if (s_last && warp == 0) {
             __threadfence();
-            double tot[4] = {0, 0, 0, 0};
-            for (int i = lane; i < I.nseg; i += 32)
-#pragma unroll
-                for (int k = 0; k < 4; k++) tot[k] += __ldcg(&I.part[i * 4 + k]);
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], off);
+            double tot[4];
+            sum_slots(I.part, I.nseg, tot, T(0));
             if (lane == 0) {
                 I.s->counter = 0u;
                 finish_iteration(I.s, I.s->iter, tot);
