@@ -42,8 +42,10 @@ constexpr int CT = 512;                 // threads per CTA (batched phases)
 constexpr int CW = CT / 32;
 constexpr int CTC = 512;                // threads per CTA of the cooperative solve (two per SM: one
 constexpr int CWC = CTC / 32;           //   1024-thread CTA per SM measured slower, 28.7 against 26.5 us)
-constexpr int UNR = 2;                  // unknowns a thread keeps in flight (FP64)
-constexpr int UNR32 = 2;                // the same in FP32
+constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP64; 256^3: 46.3
+                                        //   us per iteration against 49.3 us with 2)
+constexpr int UNR32 = 1;                // the same in FP32 (256^3: 17.9 us per iteration against
+                                        //   18.9 / 20.2 / 22.8 us with 2 / 3 / 4)
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
 
 
