@@ -40,8 +40,10 @@ namespace {
 
 constexpr int CT = 512;                 // threads per CTA (batched phases)
 constexpr int CW = CT / 32;
-constexpr int CTC = 512;                // threads per CTA of the cooperative solve (two per SM: one
-constexpr int CWC = CTC / 32;           //   1024-thread CTA per SM measured slower, 28.7 against 26.5 us)
+constexpr int CTC = 1024;               // threads per CTA of the cooperative solve, one CTA per SM
+constexpr int CWC = CTC / 32;           //   (256^3: 16.6 us per iteration against 17.6 us with two
+                                        //   512-thread CTAs per SM: half the barrier arrivals and
+                                        //   partial sums)
 constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP64; 256^3: 46.3
                                         //   us per iteration against 49.3 us with 2)
 constexpr int UNR32 = 1;                // the same in FP32 (256^3: 17.9 us per iteration against
@@ -365,7 +367,7 @@ template <> struct SolveScal<double> {
 };
 
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(CTC, 2) compact_cg_kernel(CompactArgs a) {
+__global__ void __launch_bounds__(CTC, 1) compact_cg_kernel(CompactArgs a) {
     // FP32: sums and scalars as float-float pairs; FP64: FP64
     using S = typename std::conditional<sizeof(T) == 4, ff, double>::type;
     __shared__ InnerScal st;
