@@ -48,6 +48,8 @@ constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP
                                         //   us per iteration against 49.3 us with 2)
 constexpr int UNR32 = 1;                // the same in FP32 (256^3: 17.9 us per iteration against
                                         //   18.9 / 20.2 / 22.8 us with 2 / 3 / 4)
+constexpr int UNB = 2;                  // unknowns in flight per thread in the batched phase
+                                        //   launches (8 list entries per thread per launch)
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
 
 
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(CT) compact_batch_a_kernel(const CompactInst *
     const CompactInst &I = insts[sg.inst];
     const InnerScal *s = I.a.s;
     if (s->stop) return;
-    constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    constexpr int UN = UNB;
     compact_phase_a<T, UN>((T *)I.a.y, (T *)I.a.r, (T *)I.a.p, (const T *)I.a.q, sg.u0 + (int)threadIdx.x, sg.u1,
                            CT, (T)s->alpha, (T)s->beta, s->iter == 0);
 }
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(CT) compact_batch_b_kernel(const CompactInst *
     InnerScal *s = I.a.s;
     if (s->stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    constexpr int UN = UNB;
     T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
     compact_phase_b<T, NDIM, UN>((const T *)I.a.r, (const T *)I.a.p, (T *)I.a.q, (const T *)I.a.val, I.a.nbr,
                                  (int)I.a.n, sg.u0 + (int)threadIdx.x, sg.u1, CT, s_pq, s_rq, s_qq, s_rr);
