@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(CTC, 1) compact_cg_kernel(CompactArgs a) {
         if (warp == 0 && ok) {
             S tot[4];
             if constexpr (sizeof(T) == 4)
-                warp_sum_pairs(reinterpret_cast<const float4 *>(a.pb) + 2LL * par * G, G, tot);
+                warp_sum_pairs<5>(reinterpret_cast<const float4 *>(a.pb) + 2LL * par * G, G, tot);
             else
                 grid_sums(a.pb + 4LL * par * G, G, tot);
             if (lane == 0) sc.finish(tot);

@@ -82,23 +82,25 @@ __device__ __forceinline__ ff ff_of(double d) {
 __device__ __forceinline__ double ff_to_double(ff a) { return isfinite(a.h) ? (double)a.h + (double)a.l : (double)a.h; }
 
 // Sum of G per-CTA pairs of four sums by one warp: pair i is the float4s
-// {hi[4]} at part[2 i] and {lo[4]} at part[2 i + 1].  Lane-strided, four
-// CTAs per lane in flight, then a butterfly; the same inputs give the same
-// bits in every lane and every CTA.
+// {hi[4]} at part[2 i] and {lo[4]} at part[2 i + 1].  Lane-strided, DEPTH
+// CTAs per lane in flight (5: a grid of one CTA per SM, 152, is read in one
+// round of loads), then a butterfly; the same inputs give the same bits in
+// every lane and every CTA.
+template <int PAIR_DEPTH = 4>
 __device__ __forceinline__ void warp_sum_pairs(const float4 *part, int G, ff (&tot)[4]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 4; k++) tot[k] = {0.f, 0.f};
-    for (int i0 = lane; i0 < G; i0 += 128) {
-        float4 h[4], l[4];
+    for (int i0 = lane; i0 < G; i0 += 32 * PAIR_DEPTH) {
+        float4 h[PAIR_DEPTH], l[PAIR_DEPTH];
 #pragma unroll
-        for (int m = 0; m < 4; m++) {
+        for (int m = 0; m < PAIR_DEPTH; m++) {
             const int i = i0 + 32 * m;
             h[m] = i < G ? __ldcg(part + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
             l[m] = i < G ? __ldcg(part + 2 * i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int m = 0; m < 4; m++) {
+        for (int m = 0; m < PAIR_DEPTH; m++) {
             tot[0] = ff_add(tot[0], {h[m].x, l[m].x});
             tot[1] = ff_add(tot[1], {h[m].y, l[m].y});
             tot[2] = ff_add(tot[2], {h[m].z, l[m].z});

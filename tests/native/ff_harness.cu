@@ -9,7 +9,8 @@
 //          n_fin x {pq, rq, qq, rr, tol2, rho0, delta2, maxrr, best} float64,
 //                  then {reliable, iter, best_iter, max_iter, stag_window} int64
 // out.bin: n_ops x 5 pairs (a+b, a-b, a*b, a/b, a+bh) and 2 pairs (b+a, b*a);
-//          32 lanes x 4 pairs {h, l} of the warp sum, one row per lane;
+//          32 lanes x 4 pairs {h, l} of the warp sum, one row per lane, for
+//          four and then five slots per lane in flight;
 //          n_fin x {alpha, beta, rho, best, maxrr} float64 and {stop, best_iter}
 //          int64 from finish_iteration_ff, then the same from finish_iteration.
 #include <cstdio>
@@ -45,10 +46,14 @@ __global__ void ops_kernel(const float4 *in, int n, ff *out) {
 }
 
 __global__ void sum_kernel(const float4 *slots, int n, ff *out) {
-    ff tot[4];
+    ff tot[4], tot5[4];
     warp_sum_pairs(slots, n, tot);
+    warp_sum_pairs<5>(slots, n, tot5);
 #pragma unroll
-    for (int k = 0; k < 4; k++) out[threadIdx.x * 4 + k] = tot[k];
+    for (int k = 0; k < 4; k++) {
+        out[threadIdx.x * 4 + k] = tot[k];
+        out[128 + threadIdx.x * 4 + k] = tot5[k];
+    }
 }
 
 __global__ void fin_kernel(const FinIn *in, int n, FinOut *out_ff, FinOut *out_d) {
@@ -118,7 +123,7 @@ int main(int argc, char **argv) {
     CK(cudaMalloc(&d_ops, sizeof(float4) * n_ops));
     CK(cudaMalloc(&d_ops_out, sizeof(ff) * 7 * n_ops));
     CK(cudaMalloc(&d_sums, sizeof(float4) * sums.size()));
-    CK(cudaMalloc(&d_sum_out, sizeof(ff) * 32 * 4));
+    CK(cudaMalloc(&d_sum_out, sizeof(ff) * 32 * 4 * 2));
     CK(cudaMalloc(&d_fin, sizeof(FinIn) * n_fin));
     CK(cudaMalloc(&d_ff, sizeof(FinOut) * n_fin));
     CK(cudaMalloc(&d_d, sizeof(FinOut) * n_fin));
@@ -132,7 +137,7 @@ int main(int argc, char **argv) {
     fin_kernel<<<(n_fin + 127) / 128, 128>>>(d_fin, n_fin, d_ff, d_d);
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
-    std::vector<ff> o_ops(7 * (size_t)n_ops), o_sum(32 * 4);
+    std::vector<ff> o_ops(7 * (size_t)n_ops), o_sum(32 * 4 * 2);
     std::vector<FinOut> o_ff(n_fin), o_d(n_fin);
     CK(cudaMemcpy(o_ops.data(), d_ops_out, sizeof(ff) * o_ops.size(), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(o_sum.data(), d_sum_out, sizeof(ff) * o_sum.size(), cudaMemcpyDeviceToHost));

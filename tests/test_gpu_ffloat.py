@@ -61,8 +61,8 @@ def run(exe, tmp, ops, slots, fin_v, fin_i):
     n, m, k = len(ops), len(slots), len(fin_v)
     o = np.frombuffer(raw, dtype=np.float32, count=n * 14).reshape(n, 7, 2)
     off = n * 14 * 4
-    s = np.frombuffer(raw, dtype=np.float32, count=32 * 8, offset=off).reshape(32, 4, 2)
-    off += 32 * 8 * 4
+    s = np.frombuffer(raw, dtype=np.float32, count=2 * 32 * 8, offset=off).reshape(2, 32, 4, 2)
+    off += 2 * 32 * 8 * 4
     fo = np.dtype([("d", "<f8", 5), ("i", "<i8", 2)])
     r_ff = np.frombuffer(raw, dtype=fo, count=k, offset=off)
     r_d = np.frombuffer(raw, dtype=fo, count=k, offset=off + k * fo.itemsize)
@@ -124,14 +124,16 @@ def test_warp_sum_of_slots(harness, tmp_path, n):
     ops = np.zeros((1, 4), np.float32)
     ops[0] = [1, 0, 1, 0]
     _, s, _, _ = run(harness, str(tmp_path), ops, slots, np.ones((1, 9)), np.array([[0, 0, 0, 10, 10]]))
-    # every lane holds the same bits
-    assert np.array_equal(s, np.broadcast_to(s[0], s.shape))
-    for k in range(4):
-        terms = [exact(h[i, k], l[i, k]) for i in range(n)]
-        want = sum(terms, Fraction(0))
-        scale = sum((abs(t) for t in terms), Fraction(0))
-        got = exact(s[0, k, 0], s[0, k, 1])
-        assert abs(got - want) <= max(n, 2) * 3 * U * U * scale, (k, float(abs(got - want) / scale))
+    for depth in range(2):  # four, then five slots per lane in flight
+        sd = s[depth]
+        # every lane holds the same bits
+        assert np.array_equal(sd, np.broadcast_to(sd[0], sd.shape))
+        for k in range(4):
+            terms = [exact(h[i, k], l[i, k]) for i in range(n)]
+            want = sum(terms, Fraction(0))
+            scale = sum((abs(t) for t in terms), Fraction(0))
+            got = exact(sd[0, k, 0], sd[0, k, 1])
+            assert abs(got - want) <= max(n, 2) * 3 * U * U * scale, (depth, k, float(abs(got - want) / scale))
 
 
 def test_scalar_update_matches_fp64(harness, tmp_path):
