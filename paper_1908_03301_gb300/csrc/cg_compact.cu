@@ -28,6 +28,7 @@
 // CTAs are read through L2 (ld.global.cg).  Every wait is bounded.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -336,6 +337,76 @@ __device__ __forceinline__ void grid_sums(const double *part, int G, double (&to
         for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
+// Phase B of the cooperative solve (one unknown in flight per thread), with
+// the table rows of this CTA's first jc chunks in shared memory: thread i of
+// CTA c owns entries k = c CTC + i + j nth, j = 0, 1, ...; for j < jc its
+// row's +e_d bonds are s_w[(j NDIM + d) CTC + i] and its neighbour indices
+// s_i[(j 2 (NDIM - 1) + m) CTC + i] (copied once per launch), so the
+// operator's dependent chain starts with a shared-memory load instead of an
+// L2 round trip.  Later chunks read the table from global memory.
+template <typename T, int NDIM>
+__device__ __forceinline__ void compact_phase_b_coop(const T *__restrict__ r, const T *p, T *__restrict__ q,
+                                                     const T *__restrict__ val, const int *__restrict__ nbr, int U,
+                                                     int tid, int nth, const T *s_w, const int *s_i, int jc,
+                                                     T &s_pq, T &s_rq, T &s_qq, T &s_rr) {
+    constexpr int NI = 2 * (NDIM - 1);
+    const long long VS = U + 1;
+    const int i = threadIdx.x;
+    int j = 0;
+    for (int k = tid; k < U; k += nth, j++) {
+        T wxp, wxm, wp[NDIM - 1];
+        int ip[NDIM - 1], im[NDIM - 1];
+        if (j < jc) {
+            wxp = s_w[(j * NDIM) * CTC + i];
+            wxm = i > 0 ? s_w[(j * NDIM) * CTC + i - 1] : (k > 0 ? __ldg(val + k - 1) : T(0));
+#pragma unroll
+            for (int d = 1; d < NDIM; d++) {
+                wp[d - 1] = s_w[(j * NDIM + d) * CTC + i];
+                ip[d - 1] = s_i[(j * NI + 2 * (d - 1)) * CTC + i];
+                im[d - 1] = s_i[(j * NI + 2 * (d - 1) + 1) * CTC + i];
+            }
+        } else {
+            wxp = __ldg(val + k);
+            wxm = k > 0 ? __ldg(val + k - 1) : T(0);
+#pragma unroll
+            for (int d = 1; d < NDIM; d++) {
+                wp[d - 1] = __ldg(val + d * VS + k);
+                ip[d - 1] = __ldg(nbr + (long long)(2 * (d - 1)) * U + k);
+                im[d - 1] = __ldg(nbr + (long long)(2 * (d - 1) + 1) * U + k);
+            }
+        }
+        const T pk = __ldcg(p + k);
+        T nb = wxp * __ldcg(p + k + 1);
+        nb = fma(wxm, __ldcg(p + (k > 0 ? k - 1 : 0)), nb);
+#pragma unroll
+        for (int d = 1; d < NDIM; d++) {
+            nb = fma(wp[d - 1], __ldcg(p + ip[d - 1]), nb);
+            const int jm = im[d - 1];
+            const int jj = jm >= 0 ? jm : ~jm;
+            const T wm = jm >= 0 ? __ldg(val + d * VS + jj) : T(0);
+            nb = fma(wm, __ldcg(p + jj), nb);
+        }
+        const T qk = pk - nb;
+        q[k] = qk;
+        const T rk = r[k];
+        s_pq = fma(pk, qk, s_pq);
+        s_rq = fma(rk, qk, s_rq);
+        s_qq = fma(qk, qk, s_qq);
+        s_rr = fma(rk, rk, s_rr);
+    }
+}
+
+// Shared memory the table may take per CTA; the rest of the SM's 256 KB
+// stays L1 cache for the gathered bonds and the -e_d weights.  256^3
+// percolation (8 chunks of 28 KB wanted): 17.3 / 16.8 / 16.6 / 16.4 / 17.8 us
+// per iteration with 0 / 56 / 112 / 168 / 224 KB; 192^3: 11.8 -> 11.1 us.
+constexpr int TAB_MAX_BYTES = 172032;
+// Bytes of shared memory one cached list chunk takes.
+template <typename T, int NDIM>
+constexpr int chunk_bytes() {
+    return CTC * (NDIM * (int)sizeof(T) + 2 * (NDIM - 1) * (int)sizeof(int));
+}
+
 // Scalars of the cooperative solve: the FP32 solve keeps them as float-float
 // pairs (InnerScalF), the FP64 solve as InnerScal.
 template <typename T> struct SolveScal;
@@ -394,6 +465,21 @@ __global__ void __launch_bounds__(CTC, 1) compact_cg_kernel(CompactArgs a) {
     const int tid = c * CTC + (int)threadIdx.x, nth = G * CTC;
     const int U = (int)a.n;
     constexpr int UN = sizeof(T) == 4 ? UNR32 : UNR;
+    // this CTA's table rows of its first jc chunks, copied once per launch
+    extern __shared__ __align__(16) unsigned char s_tab[];
+    constexpr int NI = 2 * (NDIM - 1);
+    T *s_w = reinterpret_cast<T *>(s_tab);
+    int *s_i = reinterpret_cast<int *>(s_tab + (size_t)a.jc * NDIM * CTC * sizeof(T));
+    for (int j = 0; j < a.jc; j++) {
+        const int k = tid + j * nth;
+        const bool in = k < U;
+        const long long VS = U + 1;
+#pragma unroll
+        for (int d = 0; d < NDIM; d++) s_w[(j * NDIM + d) * CTC + threadIdx.x] = in ? val[d * VS + k] : T(0);
+#pragma unroll
+        for (int m = 0; m < NI; m++) s_i[(j * NI + m) * CTC + threadIdx.x] = in ? nbr[(long long)m * U + k] : 0;
+    }
+    __syncthreads();
     unsigned goal = 0;  // arrivals the next barrier waits for (G per barrier, modulo 2^32)
     int nbar = 0;
     bool bad = false;
@@ -406,7 +492,7 @@ __global__ void __launch_bounds__(CTC, 1) compact_cg_kernel(CompactArgs a) {
         if (!grid_barrier(a.bar, goal, a.wait_ns, nbar++ == 0 && c == a.skip_cta)) bad = true;
         // ---- phase B: q = A p and the four sums ----
         T s_pq = T(0), s_rq = T(0), s_qq = T(0), s_rr = T(0);
-        compact_phase_b<T, NDIM, UN>(r, p, q, val, nbr, U, tid, U, nth, s_pq, s_rq, s_qq, s_rr);
+        compact_phase_b_coop<T, NDIM>(r, p, q, val, nbr, U, tid, nth, s_w, s_i, a.jc, s_pq, s_rq, s_qq, s_rr);
         T t4[4] = {s_pq, s_rq, s_qq, s_rr};
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -528,12 +614,31 @@ __global__ void __launch_bounds__(CT) compact_batch_b_kernel(const CompactInst *
 
 template <typename T, int NDIM>
 cudaError_t launch_cg_t(const CompactArgs &a, int grid, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * 2, st);
+    // shared memory for the table rows: as many of the CTA's chunks as fit
+    // beside the kernel's static shared memory
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, compact_cg_kernel<T, NDIM>);
+    if (e != cudaSuccess) return e;
+    const long long per_round = (long long)grid * CTC;
+    const long long chunks = (a.n + per_round - 1) / per_round;
+    const long long room = std::min((long long)optin - (long long)fa.sharedSizeBytes, (long long)TAB_MAX_BYTES);
+    const long long fit = room / chunk_bytes<T, NDIM>();
+    CompactArgs arg = a;
+    arg.jc = (int)std::max(0LL, std::min(chunks, fit));
+    const size_t dyn = (size_t)arg.jc * chunk_bytes<T, NDIM>();
+    // the attribute is the kernel's ceiling, the same for every launch, so
+    // that solves launched from several host threads cannot undercut
+    // each other's setting
+    e = cudaFuncSetAttribute(compact_cg_kernel<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * 2, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    CompactArgs arg = a;
     void *params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CTC), params, 0,
+    return cudaLaunchCooperativeKernel((const void *)compact_cg_kernel<T, NDIM>, dim3(grid), dim3(CTC), params, dyn,
                                        st);
 }
 

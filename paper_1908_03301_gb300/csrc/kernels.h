@@ -96,6 +96,8 @@ struct CompactArgs {
     int *err;               // set when a bounded wait gave up (cleared at launch)
     unsigned long long wait_ns;  // give up a grid-barrier wait after this long
     int skip_cta;           // testing: this CTA withholds its first arrival (-1: none)
+    int jc;                 // cooperative solve: list chunks (grid x CTA threads entries each)
+                            // whose table rows each CTA keeps in shared memory (set at launch)
 };
 int compact_grid(int ndim, int f32);
 // List the unknowns (cls == CLS_SPANNING) in lattice order and build their
