@@ -179,14 +179,6 @@ __global__ void compact_ell_kernel(Geom g, long long U, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------ refinement glue
-template <typename T>
-__global__ void compact_gather_kernel(long long U, const int *__restrict__ cidx, const T *__restrict__ src,
-                                      T *dst) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < U;
-         k += (long long)gridDim.x * blockDim.x)
-        dst[k] = src[cidx[k]];
-}
-
 // x += D^-1/2 y on the unknowns; a pass that ended with stop 6 still owes
 // alpha_k p_k (the recursion continues): fold it in and clear y.
 template <typename T>
@@ -704,14 +696,6 @@ cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f3
     return e;
 }
 
-cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st) {
-    const long long U = a.n;
-    if (f32)
-        compact_gather_kernel<float><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const float *)src, (float *)a.r);
-    else
-        compact_gather_kernel<double><<<nb_for(U), 256, 0, st>>>(U, a.cidx, (const double *)src, (double *)a.r);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, double *x, int f32, cudaStream_t st) {
     const long long U = a.n;

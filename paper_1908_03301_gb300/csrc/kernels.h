@@ -104,8 +104,6 @@ int compact_grid(int ndim, int f32);
 // ELL rows from the scaled lattice bonds gs (T).  cmap: L-entry scratch.
 cudaError_t compact_build(const Geom &g, const uint8_t *cls, long long U, int f32, const void *const gs[3],
                           int *cmap, int *cidx, int *nbr, void *val, cudaStream_t st);
-// r[k] = src[cidx[k]] (lattice -> list, T)
-cudaError_t launch_compact_gather(const CompactArgs &a, const void *src, int f32, cudaStream_t st);
 // x[cidx[k]] += D^-1/2 (y[k] (+ alpha p[k] when the pass ended with stop 6))
 cudaError_t launch_compact_correct(const CompactArgs &a, const double *dis, double *x, int f32, cudaStream_t st);
 cudaError_t launch_compact_cg(const CompactArgs &a, int ndim, int f32, int grid, cudaStream_t st);
@@ -173,6 +171,11 @@ struct OuterArgs {
 };
 int outer_grid_blocks(const Geom &g);
 cudaError_t launch_outer(const OuterArgs &a, cudaStream_t st);
+// The residual pass of a network solved on its list of U unknowns (cidx:
+// list -> lattice index): dead-end pressures filled, then the sums over the
+// listed nodes only, the scaled residual written to r_list (inner precision).
+// a.apply_corr must be 0 (the list's correction is its own launch).
+cudaError_t launch_outer_list(const OuterArgs &a, const int *cidx, long long U, void *r_list, cudaStream_t st);
 // Before a persistent-kernel launch that continues a recursion (iter > 0):
 // refresh the halo copies of r, q, p that the first sweep reads (r was
 // replaced by the refinement pass).  Does nothing when iter == 0.

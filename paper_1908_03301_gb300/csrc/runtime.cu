@@ -794,9 +794,9 @@ net_status outer_pass_compact(net_t *n, int f32, int apply_corr, const net_opts 
     if (apply_corr) CK(launch_compact_correct(ca, n->dis, n->x, f32, st));
     OuterArgs oa = outer_args(n, f32, 0, f32, o, 1);
     oa.allow_cont = o.refine != NET_REFINE_RESTART && apply_corr;  // correction applied above
-    CK(launch_outer(oa, st));
-    const InnerArgs ia = inner_args(n, f32);
-    CK(launch_compact_gather(ca, ia.r[0], f32, st));
+    // residual over the listed nodes only, written straight to the list
+    // (256^3 percolation: 1.11 M of 16.8 M nodes)
+    CK(launch_outer_list(oa, ca.cidx, ca.n, ca.r, st));
     return NET_OK;
 }
 
