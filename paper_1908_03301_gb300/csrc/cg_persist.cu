@@ -173,6 +173,29 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             for (; pre < S && pre < steps; pre++) producer_issue(pre - 1, first);
     }
 
+    // Halo rows of a sweep (producer lane 0): r (first sweep: from the
+    // vectors, whose values the first sweep leaves unchanged) or r, q, p
+    // copied by the neighbours during the previous sweep (parity ppar_).
+    // Neighbours across a periodic y boundary: the last CTA's last row above
+    // row 0, the first CTA's first row below ny-1.
+    auto issue_halo = [&](bool first_, int ppar_) {
+        const uint32_t rb = (uint32_t)px * 4u;
+        const bool top = c > 0 || wrap, bot = c + 1 < G || wrap;
+        const int ct = c > 0 ? c - 1 : G - 1, cb = c + 1 < G ? c + 1 : 0;
+        const int rt = row0 > 0 ? row0 - 1 : ny - 1, rbm = row1 < ny ? row1 : 0;
+        const uint32_t per = first_ ? rb : 3u * rb;
+        mbar_arrive_expect_tx(hfull, (top ? per : 0u) + (bot ? per : 0u));
+        if (first_) {
+            if (top) bulk_load(hrow(smem, 0, H_R), a.r + base + (long long)rt * px, rb, hfull);
+            if (bot) bulk_load(hrow(smem, 1, H_R), a.r + base + (long long)rbm * px, rb, hfull);
+        } else {
+            for (int arr = 0; arr < 3; arr++) {
+                if (top) bulk_load(hrow(smem, 0, arr), hb_row(a, ppar_, ct, 1, arr, G, px), rb, hfull);
+                if (bot) bulk_load(hrow(smem, 1, arr), hb_row(a, ppar_, cb, 0, arr, G, px), rb, hfull);
+            }
+        }
+    };
+    bool halo_early = false;  // the next sweep's halo copies are already in flight
     unsigned goal = 0;  // arrivals the next grid barrier waits for
     int sweep = 0;
     for (;; sweep++) {
@@ -184,28 +207,10 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
         if (warp == NCW) {
             // ---------------- producer ----------------
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            // halo rows of this sweep: r (first sweep: from the vectors, whose
-            // values the first sweep leaves unchanged) or r, q, p copied by
-            // the neighbours during the previous sweep
-            if (lane == 0) {
-                // neighbours across a periodic y boundary: the last CTA's
-                // last row above row 0, the first CTA's first row below ny-1
-                const uint32_t rb = (uint32_t)px * 4u;
-                const bool top = c > 0 || wrap, bot = c + 1 < G || wrap;
-                const int ct = c > 0 ? c - 1 : G - 1, cb = c + 1 < G ? c + 1 : 0;
-                const int rt = row0 > 0 ? row0 - 1 : ny - 1, rbm = row1 < ny ? row1 : 0;
-                const uint32_t per = first ? rb : 3u * rb;
-                mbar_arrive_expect_tx(hfull, (top ? per : 0u) + (bot ? per : 0u));
-                if (first) {
-                    if (top) bulk_load(hrow(smem, 0, H_R), a.r + base + (long long)rt * px, rb, hfull);
-                    if (bot) bulk_load(hrow(smem, 1, H_R), a.r + base + (long long)rbm * px, rb, hfull);
-                } else {
-                    for (int arr = 0; arr < 3; arr++) {
-                        if (top) bulk_load(hrow(smem, 0, arr), hb_row(a, ppar, ct, 1, arr, G, px), rb, hfull);
-                        if (bot) bulk_load(hrow(smem, 1, arr), hb_row(a, ppar, cb, 0, arr, G, px), rb, hfull);
-                    }
-                }
-            }
+            // halo rows of this sweep, unless already issued right after the
+            // last grid barrier
+            if (lane == 0 && !halo_early) issue_halo(first, ppar);
+            halo_early = false;
             __syncwarp();
             for (; pre < steps; pre++) producer_issue(pre - 1, first);
             pre = 0;
@@ -390,6 +395,19 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
             // if the solve stops instead, they are drained below
             asm volatile("fence.proxy.async.global;" ::: "memory");
             for (; pre < S && pre < steps; pre++) producer_issue(pre - 1, false);
+            // then wait for the grid barrier too and start the next sweep's
+            // halo copies (the neighbours' edge rows of this sweep): their
+            // addresses do not depend on the CG scalars, so their latency
+            // overlaps warp 0's reduction and scalar step instead of
+            // following it.  Drained below if the solve stops instead.
+            int early = 0;
+            if (lane == 0 && wait_count(a.bar_count, goal, a.wait_ns)) {
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                fence_proxy_async_smem();
+                issue_halo(false, par);
+                early = 1;
+            }
+            halo_early = __shfl_sync(0xffffffffu, early, 0) != 0;
         } else if (warp == 0) {
             // grid barrier (a CTA told to withhold its first arrival, for
             // tests of the bounded wait, does not arrive), then this CTA's own
@@ -417,9 +435,10 @@ __global__ void __launch_bounds__(NTH, 1) cg_persist_kernel(PersistArgs a) {
         __syncthreads();  // C
     }
     if (warp == NCW) {
-        // drain stages issued for a sweep that did not run
+        // drain stages and halo copies issued for a sweep that did not run
         for (long long k = P_step - pre; k < P_step; k++)
             mbar_wait_bounded(&full[(int)(k % S)], (uint32_t)(k / S) & 1u, plim);
+        if (halo_early) mbar_wait_bounded(hfull, (uint32_t)sweep & 1u, plim);
     }
     if (c == 0 && threadIdx.x == 0) {
         InnerScal out = st;
