@@ -204,14 +204,24 @@ def test_mixed_matches_fp64(ns):
     assert rm.fp64_fallback == 0
 
 
-def test_invariants_after_solve(ns):
-    dims = (200, 150)
-    gen = netgen.rng(25)
-    planes = netgen.percolate(netgen.lognormal_iid(dims, gen), 0.65, gen)
-    r, P = ns.solve(dims, planes)
+@pytest.mark.parametrize("dims,p,per,kernel", [((200, 150), 0.65, (), ""), ((200, 150), 0.65, (), "compact"),
+                                               ((40, 36, 30), 0.33, (1,), ""), ((48, 40, 36), 0.3, (), "")])
+def test_invariants_after_solve(ns, monkeypatch, dims, p, per, kernel):
+    """Flux balance, Tellegen (energy = G) and the reported largest nodal
+    imbalance against the oracle's residual of the returned pressures: for
+    the lattice kernels and for the list path, whose refinement pass sums
+    over the listed unknowns only (3D sparse networks take it by default)."""
+    if kernel:
+        monkeypatch.setenv("NETSOLVE_KERNEL", kernel)
+    gen = netgen.rng(25 + len(dims))
+    planes = netgen.percolate(netgen.lognormal_iid(dims, gen, periodic=per), p, gen)
+    with ns.Network(dims, planes, periodic=per) as net:
+        r = net.solve()
+        P = net.pressure()
+    assert r.status == ns.NET_OK and r.g_eff > 0.0
     assert rel(r.q_out, r.q_in) <= 1e-8
     assert rel(r.energy_g, r.g_eff) <= 1e-8
-    imb = oracle.residual(dims, planes, P)
+    imb = oracle.residual(dims, planes, P, periodic=per)
     assert np.max(np.abs(imb)) <= 1e-8 * max(np.max(g) for g in planes)
     assert abs(np.max(np.abs(imb)) - r.max_imbalance) <= 1e-12 + 1e-6 * r.max_imbalance
 
