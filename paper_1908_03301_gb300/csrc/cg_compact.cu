@@ -49,6 +49,9 @@ constexpr int UNR = 1;                  // unknowns a thread keeps in flight (FP
                                         //   us per iteration against 49.3 us with 2)
 constexpr int UNR32 = 1;                // the same in FP32 (256^3: 17.9 us per iteration against
                                         //   18.9 / 20.2 / 22.8 us with 2 / 3 / 4)
+constexpr int UNA = 2;                  // unknowns in flight per thread in phase A of the
+                                        //   cooperative solve (vector updates only; 256^3:
+                                        //   16.5 us per iteration against 16.75 / 16.8 with 1 / 4)
 constexpr int UNB = 2;                  // unknowns in flight per thread in the batched phase
                                         //   launches (8 list entries per thread per launch)
 constexpr int SCAN_CHUNK = 4096;        // lattice nodes per block in the compaction scan
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(CTC, 1) compact_cg_kernel(CompactArgs a) {
         const bool first = sc.iter() == 0;
         const T alpha = (T)sc.alpha(), beta = (T)sc.beta();
         // ---- phase A: finish iteration k-1 (UN unknowns in flight per thread) ----
-        compact_phase_a<T, UN>(y, r, p, q, tid, U, nth, alpha, beta, first);
+        compact_phase_a<T, UNA>(y, r, p, q, tid, U, nth, alpha, beta, first);
         goal += (unsigned)G;
         if (!grid_barrier(a.bar, goal, a.wait_ns, nbar++ == 0 && c == a.skip_cta)) bad = true;
         // ---- phase B: q = A p and the four sums ----
