@@ -1,9 +1,9 @@
 // cg_compact.cu -- the inner CG solve over a compacted list of unknowns.
 //
 // Near the percolation threshold the unknowns of the linear system (the
-// spanning clusters less their dead-end trees) are a small part of the
-// lattice: 13 % of a 256^3 network at p = 0.26.  A sweep over the lattice
-// then moves mostly zeros.  Here the unknowns are listed row by row (in 3D,
+// current-carrying backbone: the spanning clusters less their dead-end trees
+// and loops) are a small part of the lattice: 6.6 % of a 256^3 network at
+// p = 0.26.  A sweep over the lattice then moves mostly zeros.  Here the unknowns are listed row by row (in 3D,
 // rows in blocks of 8 x 8; see lattice_index);
 // each keeps its scaled bonds to the +e_d neighbours and the list indices of
 // its y and z neighbours (x neighbours are the adjacent list entries); the
@@ -23,9 +23,13 @@
 //   read back.  The FP32 solve keeps its sums and scalars as float-float
 //   pairs (ffloat.cuh; GB300's FP64 rate would put microseconds of FP64 on
 //   every iteration), the FP64 solve in FP64.
-// A thread owns the same unknowns in both phases and in every iteration, so
-// its own entries need no cross-SM visibility; neighbours' p written by other
-// CTAs are read through L2 (ld.global.cg).  Every wait is bounded.
+// One 1024-thread CTA per SM; thread i of CTA c owns the entries
+// c * 1024 + i + j * (grid * 1024), j = 0, 1, ..., the same in both phases and
+// in every iteration, so its own entries need no cross-SM visibility;
+// neighbours' p written by other CTAs are read through L2 (ld.global.cg).
+// Each CTA copies the table rows of its first chunks into shared memory once
+// per launch (phase B's dependent chain then starts with a shared load).
+// Every wait is bounded.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -13,7 +13,9 @@
 //    halo buffer indexed by sweep parity; in the next sweep the neighbours
 //    fetch those rows and rebuild p there themselves;
 //  * a producer warp streams the CTA's rows through a TMA (cp.async.bulk)
-//    pipeline and starts the next sweep's rows before the grid barrier;
+//    pipeline and starts the next sweep's rows before the grid barrier,
+//    then waits for the barrier itself and starts the next sweep's halo
+//    copies while warp 0 sums the partials;
 //    16 consumer warps own column strips and keep the march neighbours in
 //    registers, meeting only at the pipeline's mbarriers;
 //  * one grid barrier per sweep (arrivals counted, every CTA polls the
@@ -22,8 +24,8 @@
 //    The sums and the state are float-float pairs (ffloat.cuh): GB300's FP64
 //    rate would put microseconds of FP64 on every sweep's critical path.
 //    CTA 0 writes the final state back.
-// Every wait is bounded; a wait that gives up poisons the sums (the solve
-// stops as a breakdown) and sets *err.
+// Every wait is bounded; a wait that gives up ends the solve with stop code
+// 5 and sets *err.
 #include <cfloat>
 #include <cmath>
 
