@@ -117,3 +117,26 @@ def test_compact_capped_solve_resumes(ns, monkeypatch):
         b = net.solve(x0=P1)
     assert a.outer_iters == 1
     assert b.status == ns.NET_OK and rel(b.g_eff, ref.g_eff) <= G_TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_compact_beyond_shared_table_matches_persistent(ns, monkeypatch, precision):
+    """A list longer than the table rows each CTA keeps in shared memory (a
+    1400 x 1200 network: 1.68 M unknowns, eleven 1024-row chunks per CTA of
+    which ten fit in FP32 and four in FP64): the later chunks read their rows
+    from global memory.  G_eff and pressures equal those of the FP64 solve on
+    the lattice (the sweep kernel, itself pinned against the oracle)."""
+    dims = (1400, 1200)
+    gen = netgen.rng(9911)
+    planes = netgen.lognormal_iid(dims, gen)
+    with ns.Network(dims, planes) as net:
+        r_ref = net.solve(ns.make_opts(precision=ns.NET_FP64))
+        P_ref = net.pressure()
+    monkeypatch.setenv("NETSOLVE_KERNEL", "compact")
+    with ns.Network(dims, planes) as net:
+        r = net.solve(ns.make_opts(precision=precision))
+        P = net.pressure()
+    assert r.status == ns.NET_OK and r_ref.status == ns.NET_OK
+    assert rel(r.g_eff, r_ref.g_eff) <= G_TOL
+    assert np.max(np.abs(P - P_ref)) <= 1e-7
+    assert rel(r.energy_g, r.g_eff) <= 1e-8
