@@ -59,11 +59,21 @@ struct Band {
 // time about 100 nodes' worth of bytes take at an SM's share of HBM
 // bandwidth).  2D steps stage `rows` rows together: 6 copies per stage over
 // whole rows, 6 per row otherwise; 3D steps over whole padded rows copy each
-// array once (7 copies), narrower 3D patches copy row by row.
+// array once (7 copies), narrower 3D patches copy row by row.  A 2D row also
+// costs the consumer warps a fixed time whatever its width (they march the
+// rows one by one, two columns per thread): batches of equal-sized square
+// networks, 2.1 M nodes in all, swept in 86.5 / 46.2 / 33.7 / 25.2 / 21.0 us
+// per iteration at sides 64 / 128 / 256 / 512 / 1024, i.e. about 7.9 ps per
+// node plus 2.1 ns per row -- 270 nodes' worth per row, which the copies of
+// narrow whole-row stages (several rows each) do not reach.
 constexpr double kCopyCost = 100.0;
+constexpr double kRowCost2D = 270.0;
 inline double step_cost(int ndim, int w, int h, bool full_rows, int rows) {
-    const double copies = ndim == 2 ? (full_rows ? 6.0 / rows : 6.0)
-                                    : (full_rows ? 7.0 : 3.0 * (h + 2) + 4.0 * h + 1.0);
+    if (ndim == 2) {
+        const double copies = full_rows ? 6.0 / rows : 6.0;
+        return (double)w * h + std::max(kCopyCost * copies, kRowCost2D);
+    }
+    const double copies = full_rows ? 7.0 : 3.0 * (h + 2) + 4.0 * h + 1.0;
     return (double)w * h + kCopyCost * copies;
 }
 

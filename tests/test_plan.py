@@ -57,15 +57,17 @@ def run_plan(exe, ndim, f32, nsm, shape, dims_list):
 def step_cost(ndim, f32, w, h, px, x0):
     """The planner's cost of one march step: its nodes plus 100 node-equivalents
     per bulk copy.  2D stages hold several rows (one copy per array over whole
-    rows, one per row otherwise): a slot holds 2080 floats / 1040 doubles."""
+    rows, one per row otherwise): a slot holds 2080 floats / 1040 doubles.  A
+    2D row costs at least 270 node-equivalents (the consumers' fixed time per
+    row)."""
     full = x0 == 0 and w == px
     if ndim == 2:
         cap, V = (2080, 4) if f32 else (1040, 2)
         R = (cap - 2 * V) // px if full else cap // (w + 2 * V)
         R = max(1, min(16, R))
         copies = 6 / R if full else 6
-    else:
-        copies = 7 if full else 3 * (h + 2) + 4 * h + 1
+        return w * h + max(100 * copies, 270)
+    copies = 7 if full else 3 * (h + 2) + 4 * h + 1
     return w * h + 100 * copies
 
 
